@@ -1,0 +1,364 @@
+#!/usr/bin/env python3
+"""Benchmark of the multi-channel integrator's hot path on one GB300 per rank.
+
+Workload (both arms): the collider-like problem -- d = 14, K = 64 channels
+mapping 2-4 coordinates each by Breit-Wigner or power-law maps, 64 matching
+peaks with widths log-uniform in [1e-4, 1e-2], n = 100 bins per axis,
+1e7 calls per adaptation iteration.
+
+A step is one adaptation iteration: the sampling pass over 1e7 calls
+(RNG, forward map, integrand, g(p) over all 64 channels, accumulation),
+the pass result and iteration combination, grid refinement and the α update.
+`value` = calls per second of the FP32-eval path with inputs resident on the
+device (CUDA events on the library's stream, L2 flushed between steps).
+`e2e` = the same steps through the C ABI with the grid state round-tripping
+through pinned host buffers every step (host->device set_state, pass,
+refine, α, device->host get_state).  The FP64 path and unweighted-event
+generation (1e6 events) are measured in the same run and reported beside it.
+
+--impl reference times the FP64 CPU oracle (the only reference this method
+has) on bounded samples of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "VAMP calls/s at d=14, 64 ch (FP32-eval vs FP64 path); p50/p99 request latency"
+UNIT = "calls/s"
+WORKLOAD = "collider_d14_k64_n100: d=14, K=64 channels (2-4 BW/power maps each), 64 peaks, 100 bins, 1e7 calls/iteration"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def lookup_ops_per_call(pr) -> float:
+    """Algorithmic lane-operations per call charged to the roofline: the K*d
+    bin lookups of g(p), 8 lane-ops each (cell index 2, table probe 1, edge
+    probe + compare + select 3, density read + multiply 2).  Maps, integrand
+    and RNG are not charged, so the fraction is conservative."""
+    return 8.0 * pr.n_channels * pr.d
+
+
+def cpu_oracle_rate(pr, seconds: float, threads: int):
+    """Times the CPU oracle (as it stands) on a bounded sample of one pass."""
+    from oracle import oracle as O
+    O.build()
+    o = O.Oracle(pr)
+    n = 20_000
+    t = time.perf_counter()
+    o.sample_pass(n, 0, n_threads=threads)
+    dt = time.perf_counter() - t
+    n2 = int(max(20_000, min(5e7, n * seconds / max(dt, 1e-3))))
+    t = time.perf_counter()
+    r = o.sample_pass(n2, 1, n_threads=threads)
+    dt2 = time.perf_counter() - t
+    return r.n_calls / dt2, r.n_calls, dt2
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle on the host cores."""
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    from oracle import oracle as O
+    from paper_1811_09711_gb300 import problems as P
+    O.build()
+    pr = P.collider()
+    threads = os.cpu_count() or 1
+    o = O.Oracle(pr)
+    sample = int(os.environ.get("VAMP_REF_CALLS", "400000"))
+    it = 0
+    for _ in range(args.warmup):
+        o.sample_pass(sample, it, n_threads=threads)
+        o.refine_grids()
+        o.update_alpha()
+        it += 1
+    tot_calls, tot_t = 0, 0.0
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        r = o.sample_pass(sample, it, n_threads=threads)
+        o.refine_grids()
+        o.update_alpha()
+        tot_t += time.perf_counter() - t
+        tot_calls += r.n_calls
+        it += 1
+    v = tot_calls / tot_t
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "step": f"one adaptation iteration of {sample} calls (bounded sample)"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"{args.steps} oracle iterations of {sample} calls each, {threads} threads"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1811_09711_gb300 import problems as P
+    from paper_1811_09711_gb300 import vamp as V
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    V.load()
+    stream = torch.cuda.Stream(device=dev)
+    base = P.collider()
+    # independent replica per rank: its own random stream (request id)
+    pr = base.replace(request_id=rank)
+    N = pr.calls
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+
+    def timed_steps(g, n_steps, it0, fp):
+        """Runs n_steps adaptation iterations; returns per-step ms and calls."""
+        ms, calls = [], 0
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_steps)]
+        for s in range(n_steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()  # L2 flush outside the timed events
+                ev[s][0].record(stream)
+            r = g.sample_pass(N, it0 + s)
+            g.refine_grids()
+            g.update_alpha()
+            with torch.cuda.stream(stream):
+                ev[s][1].record(stream)
+            calls += r.n_calls
+        stream.synchronize()
+        for a, b in ev:
+            ms.append(a.elapsed_time(b))
+        return ms, calls, r
+
+    # ---- FP32-eval: headline -------------------------------------------------
+    g = V.Vamp(pr, precision=V.PREC_FP32_EVAL, stream=stream)
+    it = 0
+    for _ in range(args.warmup):
+        g.sample_pass(N, it)
+        g.refine_grids()
+        g.update_alpha()
+        it += 1
+    stream.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    g.profile(True)
+    ms, calls, last = timed_steps(g, args.steps, it, 1)
+    it += args.steps
+    ks = g.kernel_stats()
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    t_tot = sum(ms)
+    if ws > 1:
+        tt = torch.tensor([t_tot, float(calls)], dtype=torch.float64, device=dev)
+        mx = tt.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        sm = tt.clone()
+        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+        t_max, calls_all = float(mx[0]), float(sm[1])
+    else:
+        t_max, calls_all = t_tot, float(calls)
+    value = calls_all / (t_max / 1e3)
+    g.profile(False)
+
+    # ---- unweighted events from the adapted grids (1e6 events) ---------------
+    n_ev = pr.n_events
+    rb = V.record_bytes(pr.d)
+    rec = torch.empty(n_ev * rb, dtype=torch.uint8, device=dev)
+    g.generate(1000, rec.data_ptr(), gen_id=0)  # warm-up
+    g.profile(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        flush.zero_()
+        e0.record(stream)
+    gst = g.generate(n_ev, rec.data_ptr(), gen_id=1)
+    with torch.cuda.stream(stream):
+        e1.record(stream)
+    stream.synchronize()
+    gen_ms = e0.elapsed_time(e1)
+    gks = g.kernel_stats()
+    g.profile(False)
+
+    # ---- e2e through host buffers ---------------------------------------------
+    K, d, n = pr.n_channels, pr.d, pr.n_bins
+    h_edges = torch.empty(K * d * (n + 1), dtype=torch.float64, pin_memory=True).numpy().reshape(K, d, n + 1)
+    h_alpha = torch.empty(K, dtype=torch.float64, pin_memory=True).numpy()
+    h_shift = torch.empty(K, dtype=torch.float64, pin_memory=True).numpy()
+    st0 = g.get_state()
+    h_edges[...] = st0["edges"]
+    h_alpha[...] = st0["alpha"]
+    h_shift[...] = st0["shift"]
+    wmax = st0["w_max"]
+    e2e_steps = max(1, min(args.steps, 5))
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_calls = 0
+    for s in range(e2e_steps):
+        g.set_state(h_edges, h_alpha, h_shift, wmax)
+        r = g.sample_pass(N, it)
+        g.refine_grids()
+        g.update_alpha()
+        st = g.get_state()
+        h_edges[...] = st["edges"]
+        h_alpha[...] = st["alpha"]
+        h_shift[...] = st["shift"]
+        wmax = st["w_max"]
+        e2e_calls += r.n_calls
+        it += 1
+    e2e_t = time.perf_counter() - t0
+    bytes_state = 8 * (K * d * (n + 1) + 2 * K + 1)
+    e2e = {"value": e2e_calls * ws / e2e_t, "unit": UNIT,
+           "h2d_bytes_per_step": bytes_state, "d2h_bytes_per_step": bytes_state + 64}
+
+    # ---- FP64 path (same workload, same launch shape) --------------------------
+    g64 = V.Vamp(pr, precision=V.PREC_FP64, stream=stream)
+    st = g.get_state()
+    g64.set_state(st["edges"], st["alpha"], st["shift"], st["w_max"])
+    g64.sample_pass(N, it)
+    stream.synchronize()
+    f64_steps = max(1, min(args.steps, 3))
+    ms64, calls64, _ = timed_steps(g64, f64_steps, it + 1, 0)
+    fp64_rate = calls64 / (sum(ms64) / 1e3)
+
+    # ---- roofline of the dominant kernel (FP32-eval sampling kernel) ----------
+    peaks, src = _peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak_tops = n_sm * 128 * sm_max * 1e6 / 1e12  # lane-ops/s: 4 schedulers x 32 lanes per SM
+    k_ms = ks["sample_ms"] / max(ks["sample_launches"], 1)
+    ops = lookup_ops_per_call(pr) * (calls / max(args.steps, 1))
+    achieved = ops / (k_ms / 1e3) / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "Tops/s",
+            "frac": achieved / peak_tops, "traffic": None,
+            "kernel": "k_sample<float>", "kernel_ms": k_ms,
+            "peak_source": f"{n_sm} SMs x 128 lanes x {sm_max:.0f} MHz ({src} max clock)"}
+
+    res = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32-eval/f64-accumulate", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "calls_per_step": calls / args.steps,
+                      "parallelism": f"replicas{ws}", "l2": "flushed (256 MB write) between timed steps",
+                      "precision": "FP32-eval"},
+           "fp64_path": {"value": fp64_rate, "unit": UNIT, "speedup_fp32_eval": value / ws / fp64_rate},
+           "generation": {"events": gst["n_written"], "events_per_s": gst["n_written"] / (gen_ms / 1e3),
+                          "calls_used": gst["n_calls_used"], "overweight": gst["n_overweight"],
+                          "gen_kernel_ms": gks["gen_ms"], "batches": gks["gen_launches"]},
+           "last_pass": {"integral": last.integral, "sigma": math.sqrt(max(last.variance, 0.0)),
+                         "efficiency": last.efficiency, "combined": last.combined,
+                         "combined_sigma": last.combined_sigma, "chi2_dof": last.chi2_dof},
+           "e2e": e2e, "gpu_launches": 5 * args.steps, "roofline": roof, "clocks": clk}
+    if rank == 0 and not args.no_cpu_baseline and ws == 1:
+        thr = os.cpu_count() or 1
+        v, ncall, dt = cpu_oracle_rate(base, args.cpu_seconds, thr)
+        res["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": thr, "kind": "oracle",
+                               "sample": f"one oracle pass of {ncall} calls of the same workload ({dt:.1f} s)"}
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=12)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,225 @@
+/*
+ * vamp.h -- C ABI of the GB300 (sm_103a) library for the data-parallel hot
+ * path of the doubly adaptive multi-channel Monte-Carlo integrator (VAMP) of
+ * arXiv:1811.09711.
+ *
+ * The library integrates f over the unit hypercube [0,1]^d with K phase-space
+ * channels φ_c, each carrying its own adaptive VEGAS grid G_c (§3.2, §3.5):
+ *
+ *     I = Σ_c α_c ∫ f(p) / g(p) dr_c,   p = φ_c(G_c^{-1}(r_c)),        (Eq. 28)
+ *     g(p) = Σ_c α_c g_c(x_c) / φ'_c(x_c),   x_c = φ_c^{-1}(p).        (Eq. 30)
+ *
+ * and turns the adapted grids into unweighted events by rejection against the
+ * maximum weight (§2, Eq. 2; §3.5, last paragraph).
+ *
+ * Conventions shared by every entry point:
+ *   - Every function returns a vamp_status; none aborts, traps or exits.
+ *     vamp_last_error() gives a message for the last failure on a context.
+ *   - All GPU work is enqueued on the CUDA stream given to vamp_create (NULL
+ *     = the legacy default stream).  Entry points that hand results back in
+ *     host memory synchronise that stream before returning.
+ *   - A context owns every device buffer it uses (grids, α, accumulators,
+ *     generation staging); inputs are copied at create time.  Event records
+ *     are written into caller-owned device memory.
+ *   - Arrays are row-major.  Grid edges are [K][d][n+1] (ξ_{c,k,j}), bin
+ *     d-values [K][d][n], per-channel arrays [K].
+ *   - Random numbers: Philox4x32-10 (Salmon et al., SC'11) keyed by
+ *     (seed low word, seed high word); counter (call, word block, stream
+ *     field, request id); word w of a call is lane w%4 of block w/4.
+ *     Integration pass `iteration` uses stream field = iteration (< 2^31);
+ *     generation batch b of call gen_id uses 0x80000000 | gen_id<<16 | b.
+ *     A pass is therefore reproducible and independent of launch shape (§4.4).
+ *   - Limits: 1 <= d <= 16, 1 <= n_bins <= 256, 1 <= K, at most 4 mapped
+ *     coordinates per channel or peak, at most 2^32-1 calls per pass.
+ */
+#ifndef VAMP_H
+#define VAMP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    VAMP_OK = 0,
+    VAMP_ERR_INVALID_ARG = 1, /* bad pointer, size or descriptor */
+    VAMP_ERR_OOM = 2,         /* device or host allocation failed */
+    VAMP_ERR_CUDA = 3,        /* a CUDA runtime call failed (message has the name) */
+    VAMP_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up */
+    VAMP_ERR_NUMERIC = 5,     /* a non-finite weight was seen (the call still completed) */
+    VAMP_ERR_STATE = 6        /* call out of order, e.g. refine before any pass */
+} vamp_status;
+
+typedef enum {
+    VAMP_PREC_FP64 = 0,      /* maps, integrand and g(p) in FP64 */
+    VAMP_PREC_FP32_EVAL = 1  /* maps, integrand and g(p) in FP32; sums, grids, α in FP64 */
+} vamp_precision;
+
+typedef enum { VAMP_MAP_ID = 0, VAMP_MAP_BW = 1, VAMP_MAP_POW = 2 } vamp_map_kind;
+
+typedef enum { VAMP_GAUSS_NORM_REAL_LINE = 0, VAMP_GAUSS_NORM_UNIT = 1 } vamp_gauss_norm;
+
+/* One channel map φ_c, or one integrand peak (same shape).  Slot s <
+ * n_mapped maps coordinate coord[s]; all other coordinates are identity.
+ *   VAMP_MAP_BW : Breit-Wigner, a = mass m, b = width Γ > 0;
+ *                 p = m + Γ tan(A x - atan(m/Γ)), A = atan((1-m)/Γ) + atan(m/Γ),
+ *                 density 1/φ' = Γ / (A ((p-m)^2 + Γ^2)).
+ *   VAMP_MAP_POW: power law; as a channel map p = x^5 (density 0.2 p^-0.8);
+ *                 as an integrand factor (p+δ)^-0.8 / (5((1+δ)^0.2 - δ^0.2)),
+ *                 b = δ >= 0.
+ * Coordinates within one descriptor are distinct. */
+typedef struct {
+    int32_t n_mapped;
+    int32_t coord[4];
+    int32_t kind[4];
+    double a[4];
+    double b[4];
+} vamp_map_desc;
+
+/* Problem and adaptation settings (all pointers are host memory, read during
+ * vamp_create only).
+ * Integrand (synthetic stand-in for the matrix element, §3.1):
+ *   f(p) = Σ_q peak_weight[q] Π_k ( k mapped by peak q ? factor_q(p_k) : G(p_k) )
+ *   G = Gaussian(gauss_centre, gauss_sigma) normalised on the real line or on
+ *   [0,1] (gauss_norm); gauss_sigma = 0 makes G = 1. */
+typedef struct {
+    int32_t d;                  /* dimensions, 1..16 */
+    int32_t n_channels;         /* K >= 1 */
+    int32_t n_bins;             /* bins per axis n, 1..256 */
+    const vamp_map_desc *channels; /* [K] */
+    int32_t n_peaks;            /* >= 1 */
+    const double *peak_weight;  /* [n_peaks] */
+    const vamp_map_desc *peaks; /* [n_peaks] */
+    double gauss_sigma;
+    double gauss_centre;
+    int32_t gauss_norm;         /* vamp_gauss_norm */
+    uint64_t seed;              /* Philox key */
+    uint32_t request_id;        /* Philox counter word 3 */
+    double grid_alpha;          /* power α of the rebinning measure (Eq. 14), e.g. 1.5 */
+    double beta;                /* power β of the channel-weight update (Eq. 25), e.g. 0.5 */
+    int64_t n_min;              /* lower threshold of calls per live channel, e.g. 10 */
+    int32_t smooth;             /* 1: 3-point average of the bin d-values before Eq. 14 */
+    int32_t omega_mode;         /* ω_c of Eq. 25: 0 = channel variance V_c, 1 = second moment */
+    int64_t gen_batch;          /* calls per generation batch (0 = 2^20), <= 2^24 */
+    int32_t combine_from;       /* passes with iteration >= this enter the combination */
+    int32_t precision;          /* vamp_precision */
+} vamp_config;
+
+/* Result of one sampling pass (§3.1 Eqs. 10-11 per channel, Eq. 23 overall).
+ *   integral  = Σ_c α_c I_c, I_c = mean weight of channel c's calls
+ *   variance  = Σ_c α_c^2 V_c / N_c (squared error of `integral`)
+ *   w_max     = largest weight of the pass, efficiency = integral / w_max (Eq. 2)
+ *   combined, combined_sigma, chi2_dof: inverse-variance combination of the
+ *   passes with iteration >= combine_from (0 while there are none). */
+typedef struct {
+    double integral;
+    double variance;
+    double w_max;
+    double efficiency;
+    int64_t n_calls;
+    double combined;
+    double combined_sigma;
+    double chi2_dof;
+} vamp_pass_result;
+
+typedef struct vamp_ctx vamp_ctx;
+
+/* Creates a context on the current CUDA device: uniform grids ξ_j = j/n and
+ * α_c = 1/K (§3.4, §3.5).  Copies the descriptors; allocates device state.
+ * cuda_stream: a cudaStream_t (may be NULL).  Errors: INVALID_ARG (bad
+ * descriptor), OOM, CUDA.  *out is NULL on failure. */
+vamp_status vamp_create(const vamp_config *cfg, void *cuda_stream, vamp_ctx **out);
+
+/* One importance-sampling pass with the current grids and α (§3.5 work
+ * order): N_c = max(n_min, floor(α_c n_calls)) calls per live channel; each
+ * call maps r -> x_c -> p, evaluates f, inverts every other channel for g(p),
+ * and accumulates w = f/g into per-channel sums, the bin d-values
+ * D_{c,k,j} = Σ w^2 (Eq. 15) and the maximum weight.  `iteration` (< 2^31)
+ * selects the random stream.  `out` (host) is required; the call
+ * synchronises the stream.  NUMERIC if a weight was not finite. */
+vamp_status vamp_sample_pass(vamp_ctx *ctx, int64_t n_calls, uint32_t iteration,
+                             vamp_pass_result *out);
+
+/* Rebins every (channel, axis) grid from the last pass's d-values (Eqs. 14,
+ * 15): ω_j = sqrt(D_j), r_j = ω_j / Σ ω, m_j = ((r_j - 1)/ln r_j)^grid_alpha;
+ * new edges invert the cumulative of m, linear inside each old bin.
+ * Asynchronous.  STATE if no pass has run. */
+vamp_status vamp_refine_grids(vamp_ctx *ctx);
+
+/* Channel-weight update α_c <- α_c ω_c^β / Σ α ω^β (Eq. 25) from the last
+ * pass.  Channels without variance keep α_c; channels whose calls all gave
+ * w = 0 are switched off.  Asynchronous.  STATE if no pass has run. */
+vamp_status vamp_update_alpha(vamp_ctx *ctx);
+
+/* Unweighted events from the current grids and α (§3.5 last paragraph):
+ * batches of gen_batch calls, channel drawn with probability α_c, accept
+ * iff u w_max < w.  w_max starts at the last pass's maximum and is raised
+ * to the batch maximum between batches.  The first n_events accepted events
+ * in call order are written to dev_records (device memory, caller-owned,
+ * n_events * vamp_record_bytes(d) bytes, 8-byte aligned): record i =
+ * { float p[d]; zero padding to 8 bytes; double w }.  Outputs (host): events
+ * written, calls consumed up to the last written event, overweight events
+ * (w > w_max) among them.  Synchronises.  STATE if no pass has run;
+ * TIMEOUT if 65536 batches did not yield n_events. */
+vamp_status vamp_generate(vamp_ctx *ctx, int64_t n_events, uint32_t gen_id, void *dev_records,
+                          int64_t *n_written, int64_t *n_calls_used, int64_t *n_overweight);
+
+/* Bytes of one event record for dimension d: round_up(4 d, 8) + 8. */
+int64_t vamp_record_bytes(int32_t d);
+
+/* Copies the state to host arrays (any may be NULL): edges [K][d][n+1],
+ * alpha [K], per-channel shifts [K] (previous pass means), w_max.
+ * Synchronises.  Used for checkpoints and tests. */
+vamp_status vamp_get_state(vamp_ctx *ctx, double *edges, double *alpha, double *shift,
+                           double *w_max);
+
+/* Overwrites the state from host arrays (NULL = keep).  Edges must be
+ * strictly increasing from 0 to 1 on every row, α >= 0 with Σ α > 0.
+ * Marks the context as having run a pass (so refine/generate are allowed).
+ * Synchronises. */
+vamp_status vamp_set_state(vamp_ctx *ctx, const double *edges, const double *alpha,
+                           const double *shift, double w_max);
+
+/* Copies the last pass's per-channel data to host (any may be NULL): bin
+ * d-values D [K][d][n], channel means I_c [K], variances V_c [K], calls
+ * N_c [K].  Synchronises. */
+vamp_status vamp_get_pass(vamp_ctx *ctx, double *D, double *Ic, double *Vc, int64_t *Nc);
+
+/* Diagnostic: evaluates `count` single calls without accumulating, into host
+ * arrays (any but fgwc may be NULL): x [count][d] channel coordinates,
+ * p [count][d], jf [count][d] forward bins, bins [count][K][d] bin of every
+ * channel's lookup (-1 for channels with α = 0), fgwc [count][4] =
+ * {f, g, w, channel}.  mode 0: call `call0 + i` of the integration stream
+ * `field` with the channel from the allocation of the last pass (or of
+ * vamp_allocate); mode 1: generation call with the channel drawn from α.
+ * Allocates temporary device memory; synchronises. */
+vamp_status vamp_eval_calls(vamp_ctx *ctx, int32_t mode, uint32_t field, uint32_t call0,
+                            int32_t count, double *x, double *p, int32_t *jf, int32_t *bins,
+                            double *fgwc);
+
+/* Computes the call allocation N_c for n_calls without sampling (used with
+ * vamp_eval_calls).  Returns the total in *n_total.  Synchronises. */
+vamp_status vamp_allocate(vamp_ctx *ctx, int64_t n_calls, int64_t *n_total);
+
+/* Kernel timing for benchmarks: with enable = 1 the context records CUDA
+ * events on its stream around every launch of the sampling kernel and of the
+ * generation kernel; vamp_kernel_stats returns the summed device time (ms)
+ * and the launch counts since the last enable.  Off by default. */
+vamp_status vamp_profile(vamp_ctx *ctx, int32_t enable);
+vamp_status vamp_kernel_stats(vamp_ctx *ctx, double *sample_ms, int64_t *sample_launches, double *gen_ms,
+                              int64_t *gen_launches);
+
+/* Releases all device and host memory of the context (NULL is allowed). */
+void vamp_destroy(vamp_ctx *ctx);
+
+/* Message of the last failure on ctx (never NULL; empty when none). */
+const char *vamp_last_error(const vamp_ctx *ctx);
+
+/* Static name of a status code. */
+const char *vamp_status_string(vamp_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VAMP_H */

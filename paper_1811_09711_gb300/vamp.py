@@ -1,0 +1,287 @@
+"""Thin ctypes binding of the C ABI in ``include/vamp.h``.
+
+Argument marshalling only: every step of the integration runs in the CUDA
+kernels of ``libvamp_gb300.so``.  There is no CPU fallback -- if the library
+is missing or no GPU is present, :func:`load` raises.
+
+PyTorch is used only for device memory (event-record buffers) and streams.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+VAMP_OK, VAMP_ERR_INVALID_ARG, VAMP_ERR_OOM, VAMP_ERR_CUDA, VAMP_ERR_TIMEOUT, \
+    VAMP_ERR_NUMERIC, VAMP_ERR_STATE = range(7)
+PREC_FP64, PREC_FP32_EVAL = 0, 1
+
+_lock = threading.Lock()
+_lib = None
+
+
+class VampError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_STATUS = {0: "VAMP_OK", 1: "VAMP_ERR_INVALID_ARG", 2: "VAMP_ERR_OOM", 3: "VAMP_ERR_CUDA",
+           4: "VAMP_ERR_TIMEOUT", 5: "VAMP_ERR_NUMERIC", 6: "VAMP_ERR_STATE"}
+
+
+class MapDesc(C.Structure):
+    _fields_ = [("n_mapped", C.c_int32), ("coord", C.c_int32 * 4), ("kind", C.c_int32 * 4),
+                ("a", C.c_double * 4), ("b", C.c_double * 4)]
+
+
+class Config(C.Structure):
+    _fields_ = [
+        ("d", C.c_int32), ("n_channels", C.c_int32), ("n_bins", C.c_int32),
+        ("channels", C.POINTER(MapDesc)),
+        ("n_peaks", C.c_int32),
+        ("peak_weight", C.POINTER(C.c_double)),
+        ("peaks", C.POINTER(MapDesc)),
+        ("gauss_sigma", C.c_double), ("gauss_centre", C.c_double), ("gauss_norm", C.c_int32),
+        ("seed", C.c_uint64), ("request_id", C.c_uint32),
+        ("grid_alpha", C.c_double), ("beta", C.c_double), ("n_min", C.c_int64),
+        ("smooth", C.c_int32), ("omega_mode", C.c_int32),
+        ("gen_batch", C.c_int64), ("combine_from", C.c_int32), ("precision", C.c_int32),
+    ]
+
+
+class PassResult(C.Structure):
+    _fields_ = [("integral", C.c_double), ("variance", C.c_double), ("w_max", C.c_double),
+                ("efficiency", C.c_double), ("n_calls", C.c_int64), ("combined", C.c_double),
+                ("combined_sigma", C.c_double), ("chi2_dof", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+    def __repr__(self):
+        return f"PassResult({self.as_dict()})"
+
+
+def load():
+    """Build (if stale) and load the CUDA library; raise if unusable."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if not os.path.exists(path) or os.environ.get("VAMP_REBUILD"):
+            path = _build.build()
+        lib = C.CDLL(path)
+        vp, i32, i64, u32, dbl = C.c_void_p, C.c_int32, C.c_int64, C.c_uint32, C.c_double
+        st = C.c_int
+        lib.vamp_create.argtypes = [C.POINTER(Config), vp, C.POINTER(vp)]
+        lib.vamp_create.restype = st
+        lib.vamp_sample_pass.argtypes = [vp, i64, u32, C.POINTER(PassResult)]
+        lib.vamp_sample_pass.restype = st
+        lib.vamp_refine_grids.argtypes = [vp]
+        lib.vamp_refine_grids.restype = st
+        lib.vamp_update_alpha.argtypes = [vp]
+        lib.vamp_update_alpha.restype = st
+        lib.vamp_generate.argtypes = [vp, i64, u32, vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)]
+        lib.vamp_generate.restype = st
+        lib.vamp_record_bytes.argtypes = [i32]
+        lib.vamp_record_bytes.restype = i64
+        lib.vamp_get_state.argtypes = [vp, vp, vp, vp, C.POINTER(dbl)]
+        lib.vamp_get_state.restype = st
+        lib.vamp_set_state.argtypes = [vp, vp, vp, vp, dbl]
+        lib.vamp_set_state.restype = st
+        lib.vamp_get_pass.argtypes = [vp, vp, vp, vp, vp]
+        lib.vamp_get_pass.restype = st
+        lib.vamp_eval_calls.argtypes = [vp, i32, u32, u32, i32, vp, vp, vp, vp, vp]
+        lib.vamp_eval_calls.restype = st
+        lib.vamp_allocate.argtypes = [vp, i64, C.POINTER(i64)]
+        lib.vamp_allocate.restype = st
+        lib.vamp_profile.argtypes = [vp, i32]
+        lib.vamp_profile.restype = st
+        lib.vamp_kernel_stats.argtypes = [vp, C.POINTER(dbl), C.POINTER(i64), C.POINTER(dbl), C.POINTER(i64)]
+        lib.vamp_kernel_stats.restype = st
+        lib.vamp_destroy.argtypes = [vp]
+        lib.vamp_destroy.restype = None
+        lib.vamp_last_error.argtypes = [vp]
+        lib.vamp_last_error.restype = C.c_char_p
+        lib.vamp_status_string.argtypes = [st]
+        lib.vamp_status_string.restype = C.c_char_p
+        _lib = lib
+        return lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _map_array(ms) -> C.Array:
+    arr = (MapDesc * len(ms))()
+    for q in range(len(ms)):
+        r = arr[q]
+        r.n_mapped = int(ms.n_mapped[q])
+        for s in range(4):
+            r.coord[s] = int(ms.coord[q, s])
+            r.kind[s] = int(ms.kind[q, s])
+            r.a[s] = float(ms.a[q, s])
+            r.b[s] = float(ms.b[q, s])
+    return arr
+
+
+def make_config(problem, precision: int = PREC_FP64):
+    """vamp_config for a problem (see ``problems.Problem``); returns the
+    struct and the host arrays it points into (keep both alive)."""
+    ch = _map_array(problem.channels)
+    pk = _map_array(problem.peaks)
+    w = np.ascontiguousarray(problem.peak_weight, np.float64)
+    cfg = Config(int(problem.d), int(problem.n_channels), int(problem.n_bins),
+                 C.cast(ch, C.POINTER(MapDesc)), int(problem.n_peaks),
+                 w.ctypes.data_as(C.POINTER(C.c_double)), C.cast(pk, C.POINTER(MapDesc)),
+                 float(problem.gauss_sigma), float(problem.gauss_centre), int(problem.gauss_norm),
+                 int(problem.seed) & (2**64 - 1), int(problem.request_id) & 0xffffffff,
+                 float(problem.grid_alpha), float(problem.beta), int(problem.n_min),
+                 int(problem.smooth), int(problem.omega_mode), int(problem.gen_batch),
+                 int(problem.combine_from), int(precision))
+    return cfg, (ch, pk, w)
+
+
+def record_bytes(d: int) -> int:
+    return int(load().vamp_record_bytes(int(d)))
+
+
+class Vamp:
+    """One integration context on the current CUDA device.
+
+    ``stream``: a ``torch.cuda.Stream`` (or an integer cudaStream_t, or None
+    for the legacy default stream).
+    """
+
+    def __init__(self, problem, precision: int = PREC_FP64, stream=None):
+        self.lib = load()
+        self.problem = problem
+        self.d, self.K, self.n = int(problem.d), int(problem.n_channels), int(problem.n_bins)
+        self.precision = precision
+        if stream is not None and hasattr(stream, "cuda_stream"):
+            self._stream_obj = stream
+            stream = stream.cuda_stream
+        self.stream = int(stream or 0)
+        cfg, keep = make_config(problem, precision)
+        h = C.c_void_p()
+        rc = self.lib.vamp_create(C.byref(cfg), C.c_void_p(self.stream), C.byref(h))
+        if rc != VAMP_OK:
+            raise VampError(rc, "vamp_create failed")
+        self.h = h
+
+    def _check(self, rc):
+        if rc != VAMP_OK:
+            raise VampError(rc, self.lib.vamp_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.vamp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- hot path ----------------------------------------------------------
+    def sample_pass(self, n_calls: int, iteration: int) -> PassResult:
+        out = PassResult()
+        self._check(self.lib.vamp_sample_pass(self.h, int(n_calls), int(iteration), C.byref(out)))
+        return out
+
+    def refine_grids(self):
+        self._check(self.lib.vamp_refine_grids(self.h))
+
+    def update_alpha(self):
+        self._check(self.lib.vamp_update_alpha(self.h))
+
+    def generate(self, n_events: int, records_ptr: int, gen_id: int = 0):
+        """Writes up to n_events records to device memory at records_ptr."""
+        nw, nu, no = C.c_int64(), C.c_int64(), C.c_int64()
+        self._check(self.lib.vamp_generate(self.h, int(n_events), int(gen_id), C.c_void_p(records_ptr),
+                                           C.byref(nw), C.byref(nu), C.byref(no)))
+        return {"n_written": nw.value, "n_calls_used": nu.value, "n_overweight": no.value}
+
+    def generate_torch(self, n_events: int, gen_id: int = 0, out=None):
+        """generate() into a torch uint8 device tensor; returns (p, w, stats)
+        decoded on the host (p: float32 [n, d], w: float64 [n])."""
+        import torch
+        rb = record_bytes(self.d)
+        if out is None:
+            out = torch.empty(max(n_events, 1) * rb, dtype=torch.uint8, device="cuda")
+        st = self.generate(n_events, out.data_ptr(), gen_id)
+        raw = out[: st["n_written"] * rb].cpu().numpy()
+        return decode_records(raw, self.d) + (st,)
+
+    # -- kernel timing ---------------------------------------------------------
+    def profile(self, enable: bool = True):
+        self._check(self.lib.vamp_profile(self.h, int(bool(enable))))
+
+    def kernel_stats(self):
+        sm, sn, gm, gn = C.c_double(), C.c_int64(), C.c_double(), C.c_int64()
+        self._check(self.lib.vamp_kernel_stats(self.h, C.byref(sm), C.byref(sn), C.byref(gm), C.byref(gn)))
+        return {"sample_ms": sm.value, "sample_launches": sn.value, "gen_ms": gm.value,
+                "gen_launches": gn.value}
+
+    # -- state ---------------------------------------------------------------
+    def get_state(self):
+        e = np.zeros((self.K, self.d, self.n + 1), np.float64)
+        a = np.zeros(self.K, np.float64)
+        s = np.zeros(self.K, np.float64)
+        wm = C.c_double()
+        self._check(self.lib.vamp_get_state(self.h, _ptr(e), _ptr(a), _ptr(s), C.byref(wm)))
+        return {"edges": e, "alpha": a, "shift": s, "w_max": wm.value}
+
+    def set_state(self, edges=None, alpha=None, shift=None, w_max: float = 0.0):
+        e = None if edges is None else np.ascontiguousarray(edges, np.float64)
+        a = None if alpha is None else np.ascontiguousarray(alpha, np.float64)
+        s = None if shift is None else np.ascontiguousarray(shift, np.float64)
+        self._check(self.lib.vamp_set_state(self.h, _ptr(e), _ptr(a), _ptr(s), float(w_max)))
+
+    def get_pass(self):
+        D = np.zeros((self.K, self.d, self.n), np.float64)
+        Ic = np.zeros(self.K, np.float64)
+        Vc = np.zeros(self.K, np.float64)
+        Nc = np.zeros(self.K, np.int64)
+        self._check(self.lib.vamp_get_pass(self.h, _ptr(D), _ptr(Ic), _ptr(Vc), _ptr(Nc)))
+        return {"D": D, "Ic": Ic, "Vc": Vc, "Nc": Nc}
+
+    def allocate(self, n_calls: int) -> int:
+        t = C.c_int64()
+        self._check(self.lib.vamp_allocate(self.h, int(n_calls), C.byref(t)))
+        return t.value
+
+    def eval_calls(self, mode: int, field: int, call0: int, count: int, with_bins: bool = True):
+        d, K = self.d, self.K
+        x = np.zeros((count, d), np.float64)
+        p = np.zeros((count, d), np.float64)
+        jf = np.zeros((count, d), np.int32)
+        bins = np.zeros((count, K, d), np.int32) if with_bins else None
+        fgwc = np.zeros((count, 4), np.float64)
+        self._check(self.lib.vamp_eval_calls(self.h, int(mode), int(field), int(call0), int(count),
+                                             _ptr(x), _ptr(p), _ptr(jf), _ptr(bins), _ptr(fgwc)))
+        return {"x": x, "p": p, "jf": jf, "bins": bins, "f": fgwc[:, 0], "g": fgwc[:, 1],
+                "w": fgwc[:, 2], "channel": fgwc[:, 3].astype(np.int64)}
+
+
+def decode_records(raw: np.ndarray, d: int):
+    """Split raw event records into (p float32 [n, d], w float64 [n])."""
+    rb = ((4 * d + 7) & ~7) + 8
+    n = raw.size // rb
+    r = raw[: n * rb].reshape(n, rb)
+    p = r[:, : 4 * d].copy().view(np.float32).reshape(n, d)
+    w = r[:, rb - 8:].copy().view(np.float64).reshape(n)
+    return p, w
