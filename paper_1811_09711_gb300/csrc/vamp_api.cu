@@ -5,6 +5,7 @@
 #include "vamp_device.cuh"
 #include "vamp_internal.h"
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -24,7 +25,12 @@ struct vamp_ctx {
     int fp32 = 0;
     int combine_from = 0;
     int64_t gen_batch = 1 << 20;
-    int sample_grid = 0;
+    int sm_count = 0;
+    int tile = 1;              // channels per staged tile
+    size_t smem_pass = 0;      // dynamic shared memory of the integration pass kernel
+    size_t smem_gen = 0;       // ... of the generation pass kernel
+    int grid_pass = 0;         // persistent grid of the integration pass kernel
+    int grid_gen = 0;          // CTAs per SM x SMs for generation
     int have_pass = 0;
     Params prm{};
     void* arena = nullptr;
@@ -34,7 +40,7 @@ struct vamp_ctx {
     uint32_t* g_callidx = nullptr;
     int* g_counts = nullptr;
     long long* g_offsets = nullptr;
-    int64_t g_cap = 0;
+    int64_t g_cap = 0;            // calls (slots) the staging holds
     // kernel timing (vamp_profile)
     int prof = 0;
     cudaEvent_t ev[2] = {nullptr, nullptr};
@@ -110,12 +116,14 @@ bool check_maps(const vamp_map_desc* m, int cnt, int d, std::string& why)
 }
 
 template <typename T>
-MapRec<T> make_rec(const vamp_map_desc& r, double weight)
+MapRec<T> make_rec(const vamp_map_desc& r, double weight, double zinv, int d)
 {
     MapRec<T> o;
     std::memset(&o, 0, sizeof o);
     o.nmap = r.n_mapped;
-    o.weight = (T)weight;
+    // peak weight times Z^-(d - n_mapped): the Gaussian normalisation of the
+    // coordinates the peak does not map
+    o.wz = (T)(weight * std::pow(zinv, (double)(d - r.n_mapped)));
     for (int s = 0; s < r.n_mapped; ++s) {
         const int k = r.coord[s];
         o.mask |= 1u << k;
@@ -126,15 +134,48 @@ MapRec<T> make_rec(const vamp_map_desc& r, double weight)
             const double A = std::atan((1.0 - m) / G) + std::atan(m / G); // ∫_0^1 Γ/((p-m)²+Γ²)
             o.m[s] = (T)m;
             o.G[s] = (T)G;
+            o.invG[s] = (T)(1.0 / G);
             o.A[s] = (T)A;
+            o.GinvA[s] = (T)(G / A);
+            o.invA[s] = (T)(1.0 / A);
             o.t0[s] = (T)std::atan(m / G);
         } else if (r.kind[s] == VAMP_MAP_POW) {
             const double del = r.b[s];
             o.del[s] = (T)del;
-            o.powN[s] = (T)(5.0 * (std::pow(1.0 + del, 0.2) - std::pow(del, 0.2))); // ∫_0^1 (p+δ)^-0.8
+            // 1 / ∫_0^1 (p+δ)^-0.8 dp
+            o.invPowN[s] = (T)(1.0 / (5.0 * (std::pow(1.0 + del, 0.2) - std::pow(del, 0.2))));
         }
     }
     return o;
+}
+
+bool same_maps(const vamp_map_desc& a, const vamp_map_desc& b)
+{
+    if (a.n_mapped != b.n_mapped) return false;
+    for (int s = 0; s < a.n_mapped; ++s)
+        if (a.coord[s] != b.coord[s] || a.kind[s] != b.kind[s] || a.a[s] != b.a[s] || a.b[s] != b.b[s])
+            return false;
+    return true;
+}
+
+// Lookup-block layout for elements of `esz` bytes (see vamp_device.cuh).
+vamp::BlkLayout make_layout(int d, int n, int esz)
+{
+    vamp::BlkLayout L{};
+    const int per16 = 16 / esz;
+    L.Es = (n + 1 + per16 - 1) / per16 * per16;
+    L.Dn = (n + per16 - 1) / per16 * per16;
+    int lshift = 0;
+    while ((1 << lshift) < n) ++lshift;
+    lshift += 1;                      // two cells per bin on a uniform grid
+    if (lshift < 2) lshift = 2;
+    L.lshift = lshift;
+    L.Ts = ((1 << lshift) + 1 + 15) / 16 * 16;
+    L.off_dens = d * L.Es * esz;
+    L.off_tab = L.off_dens + d * L.Dn * esz;
+    L.off_span = L.off_tab + d * L.Ts;
+    L.bytes = (L.off_span + d + 15) / 16 * 16;
+    return L;
 }
 
 vamp_status read_head(vamp_ctx* c)
@@ -146,10 +187,13 @@ vamp_status read_head(vamp_ctx* c)
 
 vamp_status take_numeric_flag(vamp_ctx* c)
 {
-    if (c->h_head->err) {
+    const unsigned err = c->h_head->err;
+    if (err) {
         const unsigned zero = 0;
         VAMP_CK(c, cudaMemcpyAsync(&c->prm.sc->err, &zero, sizeof zero, cudaMemcpyHostToDevice, c->stream));
         VAMP_CK(c, cudaStreamSynchronize(c->stream));
+        if (err & vamp::ERR_TIMEOUT)
+            return fail(c, VAMP_ERR_TIMEOUT, "a bounded wait for staged grid data gave up; results are incomplete");
         return fail(c, VAMP_ERR_NUMERIC, "a non-finite weight was produced (counted as w = 0)");
     }
     return VAMP_OK;
@@ -224,12 +268,6 @@ vamp_status vamp_create(const vamp_config* cfg, void* cuda_stream, vamp_ctx** ou
 
     Params& pr = c->prm;
     pr.d = d; pr.K = K; pr.n = n; pr.P = P;
-    int top = 0; // highest power of two <= n - 1 (binary-lifting bin search)
-    if (n >= 2) {
-        top = 1;
-        while (top * 2 <= n - 1) top *= 2;
-    }
-    pr.top_step = top;
     pr.key0 = (uint32_t)(cfg->seed & 0xffffffffu);
     pr.key1 = (uint32_t)(cfg->seed >> 32);
     pr.request = cfg->request_id;
@@ -238,26 +276,32 @@ vamp_status vamp_create(const vamp_config* cfg, void* cuda_stream, vamp_ctx** ou
     pr.beta = cfg->beta;
     pr.smooth = cfg->smooth;
     pr.omega_mode = cfg->omega_mode;
-    pr.gauss_on = cfg->gauss_sigma > 0.0;
-    if (pr.gauss_on) {
+    // Gaussian factor exp(-(p-c)^2 / (2σ^2)) / Z as 2^-(p-c)^2 gk2 (gk2 = log2(e)/(2σ^2));
+    // σ = 0 switches it off (factor 1)
+    double zinv = 1.0;
+    if (cfg->gauss_sigma > 0.0) {
         const double s = cfg->gauss_sigma, cc = cfg->gauss_centre;
         double Z;
         if (cfg->gauss_norm == VAMP_GAUSS_NORM_REAL_LINE) Z = s * std::sqrt(2.0 * M_PI);
         else Z = s * std::sqrt(M_PI / 2.0) * (std::erf((1.0 - cc) / (s * M_SQRT2)) + std::erf(cc / (s * M_SQRT2)));
+        zinv = 1.0 / Z;
         pr.gcen = cc;
-        pr.gsig_inv = 1.0 / s;
-        pr.gZinv = 1.0 / Z;
+        pr.gk2 = M_LOG2E / (2.0 * s * s);
         pr.gcen_f = (float)cc;
-        pr.gsig_inv_f = (float)(1.0 / s);
-        pr.gZinv_f = (float)(1.0 / Z);
+        pr.gk2_f = (float)pr.gk2;
     }
+    pr.matching = P == K;
+    for (int q = 0; pr.matching && q < K; ++q)
+        if (!same_maps(cfg->channels[q], cfg->peaks[q])) pr.matching = 0;
+    pr.lay64 = make_layout(d, n, 8);
+    pr.lay32 = make_layout(d, n, 4);
 
     // one arena for all device state
     const size_t rows = (size_t)K * d;
     size_t off = 0;
     auto take = [&](size_t bytes) { const size_t o = off; off += align256(bytes); return o; };
-    const size_t o_e64 = take(rows * (n + 1) * 8), o_d64 = take(rows * n * 8);
-    const size_t o_e32 = take(rows * (n + 1) * 4), o_d32 = take(rows * n * 4);
+    const size_t o_e64 = take(rows * (n + 1) * 8);
+    const size_t o_lk64 = take((size_t)K * pr.lay64.bytes), o_lk32 = take((size_t)K * pr.lay32.bytes);
     const size_t o_al = take(K * 8), o_al32 = take(K * 4), o_sh = take(K * 8), o_ac = take(K * 8);
     const size_t o_nc = take(K * 8), o_pc = take((K + 1) * 8), o_D = take(rows * n * 8);
     const size_t o_cs = take(2 * K * 8), o_ic = take(K * 8), o_vc = take(K * 8), o_wc = take(K * 8);
@@ -270,8 +314,8 @@ vamp_status vamp_create(const vamp_config* cfg, void* cuda_stream, vamp_ctx** ou
     e = cudaMallocHost((void**)&c->h_head, sizeof(Scalars));
     if (e != cudaSuccess) { vamp_destroy(c); return VAMP_ERR_OOM; }
     char* b = (char*)c->arena;
-    pr.edges64 = (double*)(b + o_e64); pr.dens64 = (double*)(b + o_d64);
-    pr.edges32 = (float*)(b + o_e32); pr.dens32 = (float*)(b + o_d32);
+    pr.edges64 = (double*)(b + o_e64);
+    pr.lk64 = (unsigned char*)(b + o_lk64); pr.lk32 = (unsigned char*)(b + o_lk32);
     pr.alpha = (double*)(b + o_al); pr.alpha32 = (float*)(b + o_al32);
     pr.shift = (double*)(b + o_sh); pr.Acum = (double*)(b + o_ac);
     pr.Nc = (int64_t*)(b + o_nc); pr.Pc = (int64_t*)(b + o_pc); pr.D = (double*)(b + o_D);
@@ -287,10 +331,15 @@ vamp_status vamp_create(const vamp_config* cfg, void* cuda_stream, vamp_ctx** ou
         for (int j = 0; j <= n; ++j) edges[r * (n + 1) + j] = (double)j / (double)n;
     std::vector<MapRec<double>> ch64(K), pk64(P);
     std::vector<MapRec<float>> ch32(K), pk32(P);
-    for (int q = 0; q < K; ++q) { ch64[q] = make_rec<double>(cfg->channels[q], 0.0); ch32[q] = make_rec<float>(cfg->channels[q], 0.0); }
+    for (int q = 0; q < K; ++q) {
+        // with matching peaks the channel record carries the peak weight too
+        const double w = pr.matching ? cfg->peak_weight[q] : 0.0;
+        ch64[q] = make_rec<double>(cfg->channels[q], w, zinv, d);
+        ch32[q] = make_rec<float>(cfg->channels[q], w, zinv, d);
+    }
     for (int q = 0; q < P; ++q) {
-        pk64[q] = make_rec<double>(cfg->peaks[q], cfg->peak_weight[q]);
-        pk32[q] = make_rec<float>(cfg->peaks[q], cfg->peak_weight[q]);
+        pk64[q] = make_rec<double>(cfg->peaks[q], cfg->peak_weight[q], zinv, d);
+        pk32[q] = make_rec<float>(cfg->peaks[q], cfg->peak_weight[q], zinv, d);
     }
     vamp_status st = VAMP_OK;
 #define CREATE_CK(call)                                                                   \
@@ -307,10 +356,32 @@ vamp_status vamp_create(const vamp_config* cfg, void* cuda_stream, vamp_ctx** ou
     CREATE_CK(cudaMemcpyAsync((void*)pr.pk32, pk32.data(), P * sizeof(MapRec<float>), cudaMemcpyHostToDevice, c->stream));
     CREATE_CK(vamp::launch_derive(pr, c->stream));
     {
-        int bps = 0, sms = 0;
-        CREATE_CK(vamp::sample_occupancy(c->fp32, d, n, &bps));
-        CREATE_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->dev));
-        c->sample_grid = (bps > 0 ? bps : 1) * sms;
+        // channels per staged tile: two tile buffers plus the d-value
+        // accumulators within ~112 KB, so that two CTAs share an SM
+        const int S = c->fp32 ? pr.lay32.bytes : pr.lay64.bytes;
+        const size_t ds = (size_t)d * n * 8;
+        const size_t budget = 112 * 1024;
+        int tile = (int)((budget - vamp::SMEM_HEAD - ds) / (2 * (size_t)S));
+        if (tile < 1) tile = 1;
+        if (tile > K) tile = K;
+        c->tile = tile;
+        c->smem_pass = vamp::SMEM_HEAD + 2 * (size_t)tile * S + ds;
+        c->smem_gen = vamp::SMEM_HEAD + 2 * (size_t)tile * S;
+        int maxsm = 0;
+        CREATE_CK(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->dev));
+        if ((int)c->smem_pass > maxsm) { st = fail(c, VAMP_ERR_INVALID_ARG, "grid too large for shared memory"); goto create_fail; }
+        CREATE_CK(cudaFuncSetAttribute(vamp::pass_kernel(c->fp32, 0), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)c->smem_pass));
+        CREATE_CK(cudaFuncSetAttribute(vamp::pass_kernel(c->fp32, 1), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)c->smem_gen));
+        int b0 = 0, b1 = 0;
+        CREATE_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b0, vamp::pass_kernel(c->fp32, 0),
+                                                                vamp::PASS_THREADS, c->smem_pass));
+        CREATE_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, vamp::pass_kernel(c->fp32, 1),
+                                                                vamp::PASS_THREADS, c->smem_gen));
+        CREATE_CK(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->dev));
+        c->grid_pass = (b0 > 0 ? b0 : 1) * c->sm_count;
+        c->grid_gen = (b1 > 0 ? b1 : 1) * c->sm_count;
     }
     CREATE_CK(cudaStreamSynchronize(c->stream));
 #undef CREATE_CK
@@ -348,7 +419,11 @@ vamp_status vamp_sample_pass(vamp_ctx* c, int64_t n_calls, uint32_t iteration, v
     VAMP_CK(c, cudaMemsetAsync(P.csum, 0, (size_t)2 * c->K * 8, c->stream));
     VAMP_CK(c, vamp::launch_begin_pass(P, n_calls, c->stream));
     if (c->prof) VAMP_CK(c, cudaEventRecord(c->ev[0], c->stream));
-    VAMP_CK(c, vamp::launch_sample(P, c->fp32, iteration, c->sample_grid, c->stream));
+    vamp::PassArgs A{};
+    A.field = iteration;
+    A.tile = c->tile;
+    A.ntiles = (c->K + c->tile - 1) / c->tile;
+    VAMP_CK(c, vamp::launch_pass(P, c->fp32, 0, A, c->grid_pass, c->smem_pass, c->stream));
     if (c->prof) VAMP_CK(c, cudaEventRecord(c->ev[1], c->stream));
     VAMP_CK(c, vamp::launch_finish_pass(P, (int)iteration >= c->combine_from ? 1 : 0, c->stream));
     vamp_status s = read_head(c);
@@ -401,30 +476,33 @@ vamp_status vamp_generate(vamp_ctx* c, int64_t n_events, uint32_t gen_id, void* 
     DeviceGuard g(c->dev);
     const int rec = (int)vamp_record_bytes(c->d);
     const int64_t B = c->gen_batch;
-    const int64_t chunk = (int64_t)vamp::GEN_THREADS * vamp::GEN_ROUNDS;
-    const int nblocks = (int)((B + chunk - 1) / chunk);
-    if (c->g_cap < B) {
+    const int64_t chunk = (int64_t)vamp::PASS_THREADS * (c->fp32 ? vamp::CPT32 : vamp::CPT64);
+    const int64_t nchunks = (B + chunk - 1) / chunk;
+    if (c->g_cap < nchunks * chunk) {
         cudaFree(c->g_staging); cudaFree(c->g_callidx); cudaFree(c->g_counts); cudaFree(c->g_offsets);
         c->g_staging = nullptr; c->g_callidx = nullptr; c->g_counts = nullptr; c->g_offsets = nullptr;
         c->g_cap = 0;
-        const int64_t slots = (int64_t)nblocks * chunk;
+        const int64_t slots = nchunks * chunk;
         if (cudaMalloc(&c->g_staging, (size_t)slots * rec) != cudaSuccess ||
             cudaMalloc(&c->g_callidx, (size_t)slots * 4) != cudaSuccess ||
-            cudaMalloc(&c->g_counts, (size_t)nblocks * 4) != cudaSuccess ||
-            cudaMalloc(&c->g_offsets, (size_t)nblocks * 8) != cudaSuccess)
+            cudaMalloc(&c->g_counts, (size_t)nchunks * 4) != cudaSuccess ||
+            cudaMalloc(&c->g_offsets, (size_t)nchunks * 8) != cudaSuccess)
             return fail(c, VAMP_ERR_OOM, "generation staging allocation failed");
-        c->g_cap = B;
+        c->g_cap = slots;
     }
     VAMP_CK(c, vamp::launch_gen_prepare(c->prm, c->stream));
-    vamp::GenArgs G{};
+    vamp::PassArgs G{};
+    G.tile = c->tile;
+    G.ntiles = (c->K + c->tile - 1) / c->tile;
+    G.rec_bytes = rec;
     G.batch = B;
     G.chunk = chunk;
-    G.nblocks = nblocks;
-    G.rec_bytes = rec;
+    G.nchunks = nchunks;
     G.staging = c->g_staging;
     G.callidx = c->g_callidx;
     G.counts = c->g_counts;
     G.offsets = c->g_offsets;
+    const int grid = (int)std::min<int64_t>(nchunks, c->grid_gen);
     int64_t written = 0, used = 0, over = 0;
     uint32_t b = 0;
     vamp_status st = VAMP_OK;
@@ -433,8 +511,9 @@ vamp_status vamp_generate(vamp_ctx* c, int64_t n_events, uint32_t gen_id, void* 
         G.field = 0x80000000u | (gen_id << 16) | b;
         unsigned char* outp = (unsigned char*)dev_records + written * rec;
         if (c->prof) VAMP_CK(c, cudaEventRecord(c->ev[0], c->stream));
-        VAMP_CK(c, vamp::launch_gen_batch(c->prm, c->fp32, G, n_events - written, outp, c->stream));
+        VAMP_CK(c, vamp::launch_pass(c->prm, c->fp32, 1, G, grid, c->smem_gen, c->stream));
         if (c->prof) VAMP_CK(c, cudaEventRecord(c->ev[1], c->stream));
+        VAMP_CK(c, vamp::launch_gen_finish(c->prm, G, n_events - written, outp, c->stream));
         st = read_head(c);
         if (st != VAMP_OK) return st;
         if (c->prof) {

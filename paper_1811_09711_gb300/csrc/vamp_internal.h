@@ -9,24 +9,28 @@ namespace vamp {
 
 struct Params;
 
-constexpr int SAMPLE_THREADS = 256;  // threads per sampling CTA
-constexpr int REFINE_WARPS = 4;      // grid rows per refine CTA
-constexpr int GEN_THREADS = 256;     // threads per generation CTA
-constexpr int GEN_ROUNDS = 4;        // rounds of GEN_THREADS calls per generation CTA
+constexpr int PASS_THREADS = 256;  // threads per pass CTA
+constexpr int CPT32 = 2;           // calls per thread, FP32-eval pass
+constexpr int CPT64 = 1;           // calls per thread, FP64 pass
+constexpr int SMEM_HEAD = 512;     // bytes of barriers and scratch before the tile buffers
+constexpr int REFINE_WARPS = 4;    // grid rows per refine CTA
 
-// One generation batch: calls [0, batch) of stream `field`, processed in
-// chunks of `chunk` calls per CTA; accepted records land in `staging` at
-// the CTA's chunk offset, in call order.
-struct GenArgs {
+// Launch arguments of the pass kernel.  Integration: `field` = iteration.
+// Generation: calls [0, batch) of stream `field`, in chunks of `chunk` =
+// PASS_THREADS * CPT calls; accepted records of chunk b land in `staging`
+// from slot b * chunk on, in call order.
+struct PassArgs {
     uint32_t field;
+    int tile;          // channels per staged tile
+    int ntiles;        // ceil(K / tile)
+    int rec_bytes;
     int64_t batch;
     int64_t chunk;
-    int nblocks;
-    int rec_bytes;
-    unsigned char* staging;   // [batch][rec_bytes]
-    uint32_t* callidx;        // [batch]
-    int* counts;              // [nblocks]
-    long long* offsets;       // [nblocks]
+    int64_t nchunks;
+    unsigned char* staging;   // [nchunks * chunk][rec_bytes]
+    uint32_t* callidx;        // [nchunks * chunk]
+    int* counts;              // [nchunks]
+    long long* offsets;       // [nchunks]
 };
 
 struct EvalArgs {
@@ -42,15 +46,16 @@ struct EvalArgs {
 };
 
 cudaError_t launch_begin_pass(const Params& P, int64_t N, cudaStream_t s);
-cudaError_t launch_sample(const Params& P, int fp32, uint32_t iteration, int grid, cudaStream_t s);
-cudaError_t sample_occupancy(int fp32, int d, int n, int* blocks_per_sm);
+const void* pass_kernel(int fp32, int mode);
+cudaError_t launch_pass(const Params& P, int fp32, int mode, const PassArgs& A, int grid, size_t smem,
+                        cudaStream_t s);
 cudaError_t launch_finish_pass(const Params& P, int combine, cudaStream_t s);
 cudaError_t launch_derive(const Params& P, cudaStream_t s);
 cudaError_t launch_refine(const Params& P, cudaStream_t s);
 cudaError_t launch_update_alpha(const Params& P, cudaStream_t s);
 cudaError_t launch_gen_prepare(const Params& P, cudaStream_t s);
-cudaError_t launch_gen_batch(const Params& P, int fp32, const GenArgs& G, int64_t remaining,
-                             unsigned char* out, cudaStream_t s);
+cudaError_t launch_gen_finish(const Params& P, const PassArgs& G, int64_t remaining, unsigned char* out,
+                              cudaStream_t s);
 cudaError_t launch_eval(const Params& P, int fp32, const EvalArgs& A, cudaStream_t s);
 
 }  // namespace vamp

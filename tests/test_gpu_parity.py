@@ -48,6 +48,7 @@ def run_schedule(V, O, pr, iters, calls, prec=0, check=True, tol=1e-12):
     out = []
     for it in range(iters):
         comb = it >= pr.combine_from
+        s_prev = o.get_state()["shift"]  # shift s_c the pass's sums are taken about
         rg = g.sample_pass(calls, it)
         ro = o.sample_pass(calls, it, combine=comb, n_threads=NTHREADS)
         out.append((rg, ro))
@@ -62,11 +63,12 @@ def run_schedule(V, O, pr, iters, calls, prec=0, check=True, tol=1e-12):
             pg, po = g.get_pass(), o.get_pass()
             assert np.array_equal(pg["Nc"], po["Nc"])
             np.testing.assert_allclose(pg["D"], po["D"], rtol=tol, atol=tol * po["D"].max())
-            # α_c ∝ V_c^β and V_c = W_c - I_c^2 loses a factor W_c/V_c to
-            # cancellation, so α inherits tol * max_c W_c/V_c
+            # α_c ∝ V_c^β, and V_c comes from sums shifted by s_c: the
+            # difference of the shifted moments loses a factor
+            # (V_c + (I_c - s_c)^2) / V_c to cancellation, which α inherits
             live = (po["Nc"] > 1) & (po["Vc"] > 0)
-            Wc = po["Vc"][live] * (po["Nc"][live] - 1) / po["Nc"][live] + po["Ic"][live] ** 2
-            cond = float(np.max(Wc / po["Vc"][live])) if live.any() else 1.0
+            m2s = po["Vc"][live] + (po["Ic"][live] - s_prev[live]) ** 2
+            cond = float(np.max(m2s / po["Vc"][live])) if live.any() else 1.0
         if pr.adapt_grid:
             g.refine_grids()
             o.refine_grids()
