@@ -210,6 +210,31 @@ vamp_status vamp_profile(vamp_ctx *ctx, int32_t enable);
 vamp_status vamp_kernel_stats(vamp_ctx *ctx, double *sample_ms, int64_t *sample_launches, double *gen_ms,
                               int64_t *gen_launches);
 
+/* One sampling pass that allocates nothing, for callers that cannot let a
+ * library allocate memory (all device memory owned by the caller's own pool,
+ * or a path where an allocation could block or fail unpredictably).  The
+ * paper has no counterpart: it is an interface addition of this library.
+ *
+ * Same pass as vamp_sample_pass, without a context: the caller passes the
+ * problem (cfg, host memory, read during the call), the grid state in device
+ * memory -- dev_edges [K][d][n+1], dev_alpha [K], dev_shift [K] (previous
+ * pass means, zeros for a first pass), all read only -- and the outputs:
+ * dev_D_out (device, [K][d][n] bin d-values of the pass, may be NULL) and
+ * out (host).  The combination fields of *out are 0.  err_msg (optional,
+ * err_len bytes) receives a message on failure.
+ *
+ * All working arrays live in one static device array of 8 MiB that every
+ * GPU loading this library holds until the process exits; a problem that
+ * needs more (about K * d * (n+1) * 32 bytes plus small terms) is rejected
+ * with VAMP_ERR_INVALID_ARG and a message.  The call clears what must start
+ * at zero; calls that overlap on the GPU share the array and race.  The
+ * first call on a device looks up the array's device address (make it
+ * before any stream capture).  Synchronises cuda_stream. */
+vamp_status vamp_sample_pass_static(const vamp_config *cfg, const double *dev_edges, const double *dev_alpha,
+                                    const double *dev_shift, int64_t n_calls, uint32_t iteration,
+                                    void *cuda_stream, double *dev_D_out, vamp_pass_result *out,
+                                    char *err_msg, int32_t err_len);
+
 /* Releases all device and host memory of the context (NULL is allowed). */
 void vamp_destroy(vamp_ctx *ctx);
 

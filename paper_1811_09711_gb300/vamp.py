@@ -104,6 +104,9 @@ def load():
         lib.vamp_profile.restype = st
         lib.vamp_kernel_stats.argtypes = [vp, C.POINTER(dbl), C.POINTER(i64), C.POINTER(dbl), C.POINTER(i64)]
         lib.vamp_kernel_stats.restype = st
+        lib.vamp_sample_pass_static.argtypes = [C.POINTER(Config), vp, vp, vp, i64, u32, vp, vp,
+                                                C.POINTER(PassResult), C.c_char_p, i32]
+        lib.vamp_sample_pass_static.restype = st
         lib.vamp_destroy.argtypes = [vp]
         lib.vamp_destroy.restype = None
         lib.vamp_last_error.argtypes = [vp]
@@ -275,6 +278,24 @@ class Vamp:
                                              _ptr(x), _ptr(p), _ptr(jf), _ptr(bins), _ptr(fgwc)))
         return {"x": x, "p": p, "jf": jf, "bins": bins, "f": fgwc[:, 0], "g": fgwc[:, 1],
                 "w": fgwc[:, 2], "channel": fgwc[:, 3].astype(np.int64)}
+
+
+def sample_pass_static(problem, precision: int, edges_ptr: int, alpha_ptr: int, shift_ptr: int,
+                       n_calls: int, iteration: int, stream: int = 0, D_out_ptr: int = 0):
+    """vamp_sample_pass_static: one pass whose working memory is the
+    library's static device array (no allocation); device pointers in,
+    host PassResult out."""
+    lib = load()
+    cfg, keep = make_config(problem, precision)
+    out = PassResult()
+    msg = C.create_string_buffer(256)
+    rc = lib.vamp_sample_pass_static(C.byref(cfg), C.c_void_p(edges_ptr), C.c_void_p(alpha_ptr),
+                                     C.c_void_p(shift_ptr), int(n_calls), int(iteration),
+                                     C.c_void_p(stream), C.c_void_p(D_out_ptr or None), C.byref(out),
+                                     msg, 256)
+    if rc != VAMP_OK:
+        raise VampError(rc, msg.value.decode())
+    return out
 
 
 def decode_records(raw: np.ndarray, d: int):
