@@ -370,10 +370,16 @@ vamp_status vamp_create(const vamp_config* cfg, void* cuda_stream, vamp_ctx** ou
         int maxsm = 0;
         CREATE_CK(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->dev));
         if ((int)c->smem_pass > maxsm) { st = fail(c, VAMP_ERR_INVALID_ARG, "grid too large for shared memory"); goto create_fail; }
-        CREATE_CK(cudaFuncSetAttribute(vamp::pass_kernel(c->fp32, 0), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)c->smem_pass));
-        CREATE_CK(cudaFuncSetAttribute(vamp::pass_kernel(c->fp32, 1), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)c->smem_gen));
+        // the limit is per kernel, not per context: only ever raise it, so
+        // that contexts created earlier keep theirs
+        for (int mode = 0; mode < 2; ++mode) {
+            const size_t need = mode ? c->smem_gen : c->smem_pass;
+            cudaFuncAttributes fa{};
+            CREATE_CK(cudaFuncGetAttributes(&fa, vamp::pass_kernel(c->fp32, mode)));
+            if (fa.maxDynamicSharedSizeBytes < (int)need)
+                CREATE_CK(cudaFuncSetAttribute(vamp::pass_kernel(c->fp32, mode),
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need));
+        }
         int b0 = 0, b1 = 0;
         CREATE_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b0, vamp::pass_kernel(c->fp32, 0),
                                                                 vamp::PASS_THREADS, c->smem_pass));

@@ -329,3 +329,13 @@ def test_repeatable(V):
     b = V.Vamp(pr).sample_pass(500_000, 3)
     assert abs(a.integral - b.integral) <= 1e-13 * a.integral
     assert a.w_max == b.w_max
+
+
+def test_contexts_with_different_shapes_coexist(V, O):
+    """A context with a larger shared-memory need, created first, still runs
+    after a smaller one was created (the kernel limit is only raised)."""
+    big = V.Vamp(_edge_problem(16, 256, 8), precision=1)
+    small = V.Vamp(P.single_gauss(), precision=1)
+    rb = big.sample_pass(20_000, 0)
+    rs = small.sample_pass(10_000, 0)
+    assert rb.n_calls > 0 and rs.n_calls == 10_000
