@@ -1,6 +1,7 @@
-// vamp_api.cu -- the C ABI of include/vamp.h: validation, device state,
-// launch order, result read-back.  Every step of the integration runs in the
-// kernels of vamp_kernels.cu; this file only marshals.
+// vamp_api.cu -- the C ABI of include/vamp.h: contexts, launch order,
+// result read-back, and the choice of pass-kernel variant (autotuned once per
+// shape class).  Every step of the integration runs in the kernels; this file
+// only marshals.
 #include "../../include/vamp.h"
 #include "vamp_device.cuh"
 #include "vamp_internal.h"
@@ -10,12 +11,15 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
+#include <tuple>
 #include <vector>
 
-using vamp::MapRec;
 using vamp::Params;
+using vamp::PassVariant;
 using vamp::Scalars;
 
 struct vamp_ctx {
@@ -29,8 +33,9 @@ struct vamp_ctx {
     int tile = 1;              // channels per staged tile
     size_t smem_pass = 0;      // dynamic shared memory of the integration pass kernel
     size_t smem_gen = 0;       // ... of the generation pass kernel
+    const PassVariant* var = nullptr;  // pass kernels in use
     int grid_pass = 0;         // persistent grid of the integration pass kernel
-    int grid_gen = 0;          // CTAs per SM x SMs for generation
+    int grid_gen = 0;          // resident CTAs of the generation pass kernel
     int have_pass = 0;
     Params prm{};
     void* arena = nullptr;
@@ -86,98 +91,6 @@ struct DeviceGuard {
     }
 };
 
-size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
-
-bool check_maps(const vamp_map_desc* m, int cnt, int d, std::string& why)
-{
-    for (int q = 0; q < cnt; ++q) {
-        const vamp_map_desc& r = m[q];
-        if (r.n_mapped < 0 || r.n_mapped > vamp::MAXMAP) { why = "n_mapped out of range"; return false; }
-        unsigned seen = 0;
-        for (int s = 0; s < r.n_mapped; ++s) {
-            const int k = r.coord[s];
-            if (k < 0 || k >= d) { why = "mapped coordinate out of range"; return false; }
-            if (seen & (1u << k)) { why = "coordinate mapped twice"; return false; }
-            seen |= 1u << k;
-            if (r.kind[s] == VAMP_MAP_BW) {
-                if (!(r.b[s] > 0.0) || !std::isfinite(r.a[s]) || !std::isfinite(r.b[s])) {
-                    why = "Breit-Wigner width must be > 0";
-                    return false;
-                }
-            } else if (r.kind[s] == VAMP_MAP_POW) {
-                if (!(r.b[s] >= 0.0) || !std::isfinite(r.b[s])) { why = "power-law delta must be >= 0"; return false; }
-            } else if (r.kind[s] != VAMP_MAP_ID) {
-                why = "unknown map kind";
-                return false;
-            }
-        }
-    }
-    return true;
-}
-
-template <typename T>
-MapRec<T> make_rec(const vamp_map_desc& r, double weight, double zinv, int d)
-{
-    MapRec<T> o;
-    std::memset(&o, 0, sizeof o);
-    o.nmap = r.n_mapped;
-    // peak weight times Z^-(d - n_mapped): the Gaussian normalisation of the
-    // coordinates the peak does not map
-    o.wz = (T)(weight * std::pow(zinv, (double)(d - r.n_mapped)));
-    for (int s = 0; s < r.n_mapped; ++s) {
-        const int k = r.coord[s];
-        o.mask |= 1u << k;
-        o.slotpack |= (uint64_t)s << (4 * k);
-        o.kind[s] = r.kind[s];
-        if (r.kind[s] == VAMP_MAP_BW) {
-            const double m = r.a[s], G = r.b[s];
-            const double A = std::atan((1.0 - m) / G) + std::atan(m / G); // ∫_0^1 Γ/((p-m)²+Γ²)
-            o.m[s] = (T)m;
-            o.G[s] = (T)G;
-            o.invG[s] = (T)(1.0 / G);
-            o.A[s] = (T)A;
-            o.GinvA[s] = (T)(G / A);
-            o.invA[s] = (T)(1.0 / A);
-            o.t0[s] = (T)std::atan(m / G);
-        } else if (r.kind[s] == VAMP_MAP_POW) {
-            const double del = r.b[s];
-            o.del[s] = (T)del;
-            // 1 / ∫_0^1 (p+δ)^-0.8 dp
-            o.invPowN[s] = (T)(1.0 / (5.0 * (std::pow(1.0 + del, 0.2) - std::pow(del, 0.2))));
-        }
-    }
-    return o;
-}
-
-bool same_maps(const vamp_map_desc& a, const vamp_map_desc& b)
-{
-    if (a.n_mapped != b.n_mapped) return false;
-    for (int s = 0; s < a.n_mapped; ++s)
-        if (a.coord[s] != b.coord[s] || a.kind[s] != b.kind[s] || a.a[s] != b.a[s] || a.b[s] != b.b[s])
-            return false;
-    return true;
-}
-
-// Lookup-block layout for elements of `esz` bytes (see vamp_device.cuh).
-vamp::BlkLayout make_layout(int d, int n, int esz)
-{
-    vamp::BlkLayout L{};
-    const int per16 = 16 / esz;
-    L.Es = (n + 1 + per16 - 1) / per16 * per16;
-    L.Dn = (n + per16 - 1) / per16 * per16;
-    int lshift = 0;
-    while ((1 << lshift) < n) ++lshift;
-    lshift += 1;                      // two cells per bin on a uniform grid
-    if (lshift < 2) lshift = 2;
-    L.lshift = lshift;
-    L.Ts = ((1 << lshift) + 1 + 15) / 16 * 16;
-    L.off_dens = d * L.Es * esz;
-    L.off_tab = L.off_dens + d * L.Dn * esz;
-    L.off_span = L.off_tab + d * L.Ts;
-    L.bytes = (L.off_span + d + 15) / 16 * 16;
-    return L;
-}
-
 vamp_status read_head(vamp_ctx* c)
 {
     VAMP_CK(c, cudaMemcpyAsync(c->h_head, c->prm.sc, HEAD_BYTES, cudaMemcpyDeviceToHost, c->stream));
@@ -196,6 +109,81 @@ vamp_status take_numeric_flag(vamp_ctx* c)
             return fail(c, VAMP_ERR_TIMEOUT, "a bounded wait for staged grid data gave up; results are incomplete");
         return fail(c, VAMP_ERR_NUMERIC, "a non-finite weight was produced (counted as w = 0)");
     }
+    return VAMP_OK;
+}
+
+vamp::PassArgs pass_args(const vamp_ctx* c, uint32_t field)
+{
+    vamp::PassArgs A{};
+    A.field = field;
+    A.tile = c->tile;
+    A.ntiles = (c->K + c->tile - 1) / c->tile;
+    return A;
+}
+
+// Autotuner: the fastest pass-kernel variant for a shape class, measured
+// once per process on a short integration pass and then reused.
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int, int, int>, const PassVariant*> g_tuned;
+
+vamp_status choose_variant(vamp_ctx* c)
+{
+    const std::vector<const PassVariant*> cand = vamp::pass_candidates(c->fp32, c->d, c->n);
+    if (cand.empty()) return fail(c, VAMP_ERR_INVALID_ARG, "no pass kernel for this shape");
+    for (const PassVariant* v : cand) {
+        VAMP_CK(c, vamp::ensure_smem(v->fn[0], c->smem_pass));
+        VAMP_CK(c, vamp::ensure_smem(v->fn[1], c->smem_gen));
+    }
+    auto grid_of = [&](const PassVariant* v, int mode, int* grid) -> cudaError_t {
+        int b = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, v->fn[mode], vamp::PASS_THREADS,
+                                                                      mode ? c->smem_gen : c->smem_pass);
+        *grid = (b > 0 ? b : 1) * c->sm_count;
+        return e;
+    };
+    const auto key = std::make_tuple(c->dev, c->fp32, c->d, c->n, std::min(c->K, 64), c->tile);
+    const PassVariant* best = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tuned.find(key);
+        if (it != g_tuned.end()) best = it->second;
+    }
+    if (!best && cand.size() == 1) best = cand[0];
+    if (!best) {
+        // time each candidate on a short pass over the initial grids; the
+        // pass result is discarded (no finish kernel runs, state is unchanged)
+        const int64_t probe = std::max<int64_t>(1 << 18, (int64_t)c->K * 2048);
+        cudaEvent_t e0, e1;
+        VAMP_CK(c, cudaEventCreate(&e0));
+        VAMP_CK(c, cudaEventCreate(&e1));
+        float best_ms = 1e30f;
+        for (const PassVariant* v : cand) {
+            int grid = 0;
+            VAMP_CK(c, grid_of(v, 0, &grid));
+            float ms_v = 0.f;
+            for (int rep = 0; rep < 2; ++rep) {
+                VAMP_CK(c, vamp::launch_begin_pass(c->prm, probe, c->stream));
+                VAMP_CK(c, cudaEventRecord(e0, c->stream));
+                VAMP_CK(c, v->launch(c->prm, 0, pass_args(c, 0x7fffffffu), grid, c->smem_pass, c->stream));
+                VAMP_CK(c, cudaEventRecord(e1, c->stream));
+                VAMP_CK(c, cudaEventSynchronize(e1));
+                VAMP_CK(c, cudaEventElapsedTime(&ms_v, e0, e1));
+            }
+            if (ms_v < best_ms) { best_ms = ms_v; best = v; }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        // the probe touched the accumulators and scalars: clear them
+        VAMP_CK(c, cudaMemsetAsync(c->prm.D, 0, (size_t)c->K * c->d * c->n * 8, c->stream));
+        VAMP_CK(c, cudaMemsetAsync(c->prm.csum, 0, (size_t)2 * c->K * 8, c->stream));
+        VAMP_CK(c, cudaMemsetAsync(c->prm.sc, 0, HEAD_BYTES, c->stream));
+        VAMP_CK(c, cudaStreamSynchronize(c->stream));
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tuned[key] = best;
+    }
+    c->var = best;
+    VAMP_CK(c, grid_of(best, 0, &c->grid_pass));
+    VAMP_CK(c, grid_of(best, 1, &c->grid_gen));
     return VAMP_OK;
 }
 
@@ -243,153 +231,56 @@ vamp_status vamp_create(const vamp_config* cfg, void* cuda_stream, vamp_ctx** ou
 {
     if (!out) return VAMP_ERR_INVALID_ARG;
     *out = nullptr;
-    if (!cfg) return VAMP_ERR_INVALID_ARG;
-    const int d = cfg->d, K = cfg->n_channels, n = cfg->n_bins, P = cfg->n_peaks;
-    if (d < 1 || d > vamp::DMAX || K < 1 || n < 1 || n > vamp::MAX_BINS || P < 1 || !cfg->channels ||
-        !cfg->peaks || !cfg->peak_weight)
-        return VAMP_ERR_INVALID_ARG;
+    Params pr{};
+    vamp::Setup S;
     std::string why;
-    if (!check_maps(cfg->channels, K, d, why) || !check_maps(cfg->peaks, P, d, why)) return VAMP_ERR_INVALID_ARG;
-    if (!(cfg->gauss_sigma >= 0.0) || !(cfg->grid_alpha > 0.0) || !std::isfinite(cfg->beta) || cfg->n_min < 1 ||
-        cfg->gen_batch < 0 || cfg->gen_batch > (int64_t(1) << 24) ||
-        (cfg->precision != VAMP_PREC_FP64 && cfg->precision != VAMP_PREC_FP32_EVAL))
-        return VAMP_ERR_INVALID_ARG;
-    for (int q = 0; q < P; ++q)
-        if (!std::isfinite(cfg->peak_weight[q])) return VAMP_ERR_INVALID_ARG;
+    if (!vamp::build_setup(cfg, pr, S, why)) return VAMP_ERR_INVALID_ARG;
 
     vamp_ctx* c = new (std::nothrow) vamp_ctx();
     if (!c) return VAMP_ERR_OOM;
     if (cudaGetDevice(&c->dev) != cudaSuccess) { delete c; return VAMP_ERR_CUDA; }
     c->stream = (cudaStream_t)cuda_stream;
-    c->d = d; c->K = K; c->n = n; c->P = P;
-    c->fp32 = cfg->precision == VAMP_PREC_FP32_EVAL;
+    c->d = S.d; c->K = S.K; c->n = S.n; c->P = S.P;
+    c->fp32 = S.fp32;
     c->combine_from = cfg->combine_from;
     c->gen_batch = cfg->gen_batch > 0 ? cfg->gen_batch : (int64_t(1) << 20);
-
-    Params& pr = c->prm;
-    pr.d = d; pr.K = K; pr.n = n; pr.P = P;
-    pr.key0 = (uint32_t)(cfg->seed & 0xffffffffu);
-    pr.key1 = (uint32_t)(cfg->seed >> 32);
-    pr.request = cfg->request_id;
-    pr.n_min = cfg->n_min;
-    pr.grid_alpha = cfg->grid_alpha;
-    pr.beta = cfg->beta;
-    pr.smooth = cfg->smooth;
-    pr.omega_mode = cfg->omega_mode;
-    // Gaussian factor exp(-(p-c)^2 / (2σ^2)) / Z as 2^-(p-c)^2 gk2 (gk2 = log2(e)/(2σ^2));
-    // σ = 0 switches it off (factor 1)
-    double zinv = 1.0;
-    if (cfg->gauss_sigma > 0.0) {
-        const double s = cfg->gauss_sigma, cc = cfg->gauss_centre;
-        double Z;
-        if (cfg->gauss_norm == VAMP_GAUSS_NORM_REAL_LINE) Z = s * std::sqrt(2.0 * M_PI);
-        else Z = s * std::sqrt(M_PI / 2.0) * (std::erf((1.0 - cc) / (s * M_SQRT2)) + std::erf(cc / (s * M_SQRT2)));
-        zinv = 1.0 / Z;
-        pr.gcen = cc;
-        pr.gk2 = M_LOG2E / (2.0 * s * s);
-        pr.gcen_f = (float)cc;
-        pr.gk2_f = (float)pr.gk2;
-    }
-    pr.matching = P == K;
-    for (int q = 0; pr.matching && q < K; ++q)
-        if (!same_maps(cfg->channels[q], cfg->peaks[q])) pr.matching = 0;
-    pr.lay64 = make_layout(d, n, 8);
-    pr.lay32 = make_layout(d, n, 4);
-
-    // one arena for all device state
-    const size_t rows = (size_t)K * d;
-    size_t off = 0;
-    auto take = [&](size_t bytes) { const size_t o = off; off += align256(bytes); return o; };
-    const size_t o_e64 = take(rows * (n + 1) * 8);
-    const size_t o_lk64 = take((size_t)K * pr.lay64.bytes), o_lk32 = take((size_t)K * pr.lay32.bytes);
-    const size_t o_al = take(K * 8), o_al32 = take(K * 4), o_sh = take(K * 8), o_ac = take(K * 8);
-    const size_t o_nc = take(K * 8), o_pc = take((K + 1) * 8), o_D = take(rows * n * 8);
-    const size_t o_cs = take(2 * K * 8), o_ic = take(K * 8), o_vc = take(K * 8), o_wc = take(K * 8);
-    const size_t o_ch64 = take(K * sizeof(MapRec<double>)), o_ch32 = take(K * sizeof(MapRec<float>));
-    const size_t o_pk64 = take(P * sizeof(MapRec<double>)), o_pk32 = take(P * sizeof(MapRec<float>));
-    const size_t o_sc = take(sizeof(Scalars));
+    const vamp::Arena ar = vamp::plan_arena(pr);
     DeviceGuard g(c->dev);
-    cudaError_t e = cudaMalloc(&c->arena, off);
+    cudaError_t e = cudaMalloc(&c->arena, ar.bytes);
     if (e != cudaSuccess) { delete c; return e == cudaErrorMemoryAllocation ? VAMP_ERR_OOM : VAMP_ERR_CUDA; }
     e = cudaMallocHost((void**)&c->h_head, sizeof(Scalars));
     if (e != cudaSuccess) { vamp_destroy(c); return VAMP_ERR_OOM; }
-    char* b = (char*)c->arena;
-    pr.edges64 = (double*)(b + o_e64);
-    pr.lk64 = (unsigned char*)(b + o_lk64); pr.lk32 = (unsigned char*)(b + o_lk32);
-    pr.alpha = (double*)(b + o_al); pr.alpha32 = (float*)(b + o_al32);
-    pr.shift = (double*)(b + o_sh); pr.Acum = (double*)(b + o_ac);
-    pr.Nc = (int64_t*)(b + o_nc); pr.Pc = (int64_t*)(b + o_pc); pr.D = (double*)(b + o_D);
-    pr.csum = (double*)(b + o_cs); pr.Ic = (double*)(b + o_ic); pr.Vc = (double*)(b + o_vc);
-    pr.Wc = (double*)(b + o_wc);
-    pr.ch64 = (MapRec<double>*)(b + o_ch64); pr.ch32 = (MapRec<float>*)(b + o_ch32);
-    pr.pk64 = (MapRec<double>*)(b + o_pk64); pr.pk32 = (MapRec<float>*)(b + o_pk32);
-    pr.sc = (Scalars*)(b + o_sc);
+    vamp::bind_arena(pr, (unsigned char*)c->arena, ar);
+    c->prm = pr;
+    Params& P = c->prm;
 
-    // host images: uniform grids ξ_j = j/n, α_c = 1/K (§3.4, §3.5)
+    // initial state: uniform grids ξ_j = j/n, α_c = 1/K (§3.4, §3.5)
+    const int d = S.d, K = S.K, n = S.n;
+    const size_t rows = (size_t)K * d;
     std::vector<double> edges(rows * (n + 1)), alpha(K, 1.0 / (double)K);
     for (size_t r = 0; r < rows; ++r)
         for (int j = 0; j <= n; ++j) edges[r * (n + 1) + j] = (double)j / (double)n;
-    std::vector<MapRec<double>> ch64(K), pk64(P);
-    std::vector<MapRec<float>> ch32(K), pk32(P);
-    for (int q = 0; q < K; ++q) {
-        // with matching peaks the channel record carries the peak weight too
-        const double w = pr.matching ? cfg->peak_weight[q] : 0.0;
-        ch64[q] = make_rec<double>(cfg->channels[q], w, zinv, d);
-        ch32[q] = make_rec<float>(cfg->channels[q], w, zinv, d);
-    }
-    for (int q = 0; q < P; ++q) {
-        pk64[q] = make_rec<double>(cfg->peaks[q], cfg->peak_weight[q], zinv, d);
-        pk32[q] = make_rec<float>(cfg->peaks[q], cfg->peak_weight[q], zinv, d);
-    }
     vamp_status st = VAMP_OK;
 #define CREATE_CK(call)                                                                   \
     do {                                                                                  \
         cudaError_t e_ = (call);                                                          \
         if (e_ != cudaSuccess) { st = cuda_fail(c, e_, #call); goto create_fail; }        \
     } while (0)
-    CREATE_CK(cudaMemsetAsync(c->arena, 0, off, c->stream));
-    CREATE_CK(cudaMemcpyAsync(pr.edges64, edges.data(), edges.size() * 8, cudaMemcpyHostToDevice, c->stream));
-    CREATE_CK(cudaMemcpyAsync(pr.alpha, alpha.data(), K * 8, cudaMemcpyHostToDevice, c->stream));
-    CREATE_CK(cudaMemcpyAsync((void*)pr.ch64, ch64.data(), K * sizeof(MapRec<double>), cudaMemcpyHostToDevice, c->stream));
-    CREATE_CK(cudaMemcpyAsync((void*)pr.ch32, ch32.data(), K * sizeof(MapRec<float>), cudaMemcpyHostToDevice, c->stream));
-    CREATE_CK(cudaMemcpyAsync((void*)pr.pk64, pk64.data(), P * sizeof(MapRec<double>), cudaMemcpyHostToDevice, c->stream));
-    CREATE_CK(cudaMemcpyAsync((void*)pr.pk32, pk32.data(), P * sizeof(MapRec<float>), cudaMemcpyHostToDevice, c->stream));
-    CREATE_CK(vamp::launch_derive(pr, c->stream));
+    CREATE_CK(cudaMemsetAsync(c->arena, 0, ar.bytes, c->stream));
+    CREATE_CK(cudaMemcpyAsync(P.edges64, edges.data(), edges.size() * 8, cudaMemcpyHostToDevice, c->stream));
+    CREATE_CK(cudaMemcpyAsync(P.alpha, alpha.data(), K * 8, cudaMemcpyHostToDevice, c->stream));
+    CREATE_CK(vamp::upload_setup(P, S, c->stream));
+    CREATE_CK(vamp::launch_derive(P, c->stream));
+    CREATE_CK(cudaStreamSynchronize(c->stream));
     {
-        // channels per staged tile: two tile buffers plus the d-value
-        // accumulators within ~112 KB, so that two CTAs share an SM
-        const int S = c->fp32 ? pr.lay32.bytes : pr.lay64.bytes;
-        const size_t ds = (size_t)d * n * 8;
-        const size_t budget = 112 * 1024;
-        int tile = (int)((budget - vamp::SMEM_HEAD - ds) / (2 * (size_t)S));
-        if (tile < 1) tile = 1;
-        if (tile > K) tile = K;
-        c->tile = tile;
-        c->smem_pass = vamp::SMEM_HEAD + 2 * (size_t)tile * S + ds;
-        c->smem_gen = vamp::SMEM_HEAD + 2 * (size_t)tile * S;
+        vamp::pass_smem(P, c->fp32, &c->tile, &c->smem_pass, &c->smem_gen);
         int maxsm = 0;
         CREATE_CK(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->dev));
         if ((int)c->smem_pass > maxsm) { st = fail(c, VAMP_ERR_INVALID_ARG, "grid too large for shared memory"); goto create_fail; }
-        // the limit is per kernel, not per context: only ever raise it, so
-        // that contexts created earlier keep theirs
-        for (int mode = 0; mode < 2; ++mode) {
-            const size_t need = mode ? c->smem_gen : c->smem_pass;
-            cudaFuncAttributes fa{};
-            CREATE_CK(cudaFuncGetAttributes(&fa, vamp::pass_kernel(c->fp32, mode)));
-            if (fa.maxDynamicSharedSizeBytes < (int)need)
-                CREATE_CK(cudaFuncSetAttribute(vamp::pass_kernel(c->fp32, mode),
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need));
-        }
-        int b0 = 0, b1 = 0;
-        CREATE_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b0, vamp::pass_kernel(c->fp32, 0),
-                                                                vamp::PASS_THREADS, c->smem_pass));
-        CREATE_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, vamp::pass_kernel(c->fp32, 1),
-                                                                vamp::PASS_THREADS, c->smem_gen));
         CREATE_CK(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->dev));
-        c->grid_pass = (b0 > 0 ? b0 : 1) * c->sm_count;
-        c->grid_gen = (b1 > 0 ? b1 : 1) * c->sm_count;
+        st = choose_variant(c);
+        if (st != VAMP_OK) goto create_fail;
     }
-    CREATE_CK(cudaStreamSynchronize(c->stream));
 #undef CREATE_CK
     *out = c;
     return VAMP_OK;
@@ -425,11 +316,7 @@ vamp_status vamp_sample_pass(vamp_ctx* c, int64_t n_calls, uint32_t iteration, v
     VAMP_CK(c, cudaMemsetAsync(P.csum, 0, (size_t)2 * c->K * 8, c->stream));
     VAMP_CK(c, vamp::launch_begin_pass(P, n_calls, c->stream));
     if (c->prof) VAMP_CK(c, cudaEventRecord(c->ev[0], c->stream));
-    vamp::PassArgs A{};
-    A.field = iteration;
-    A.tile = c->tile;
-    A.ntiles = (c->K + c->tile - 1) / c->tile;
-    VAMP_CK(c, vamp::launch_pass(P, c->fp32, 0, A, c->grid_pass, c->smem_pass, c->stream));
+    VAMP_CK(c, c->var->launch(P, 0, pass_args(c, iteration), c->grid_pass, c->smem_pass, c->stream));
     if (c->prof) VAMP_CK(c, cudaEventRecord(c->ev[1], c->stream));
     VAMP_CK(c, vamp::launch_finish_pass(P, (int)iteration >= c->combine_from ? 1 : 0, c->stream));
     vamp_status s = read_head(c);
@@ -482,7 +369,7 @@ vamp_status vamp_generate(vamp_ctx* c, int64_t n_events, uint32_t gen_id, void* 
     DeviceGuard g(c->dev);
     const int rec = (int)vamp_record_bytes(c->d);
     const int64_t B = c->gen_batch;
-    const int64_t chunk = (int64_t)vamp::PASS_THREADS * (c->fp32 ? vamp::CPT32 : vamp::CPT64);
+    const int64_t chunk = (int64_t)vamp::PASS_THREADS * c->var->cpt;
     const int64_t nchunks = (B + chunk - 1) / chunk;
     if (c->g_cap < nchunks * chunk) {
         cudaFree(c->g_staging); cudaFree(c->g_callidx); cudaFree(c->g_counts); cudaFree(c->g_offsets);
@@ -497,9 +384,7 @@ vamp_status vamp_generate(vamp_ctx* c, int64_t n_events, uint32_t gen_id, void* 
         c->g_cap = slots;
     }
     VAMP_CK(c, vamp::launch_gen_prepare(c->prm, c->stream));
-    vamp::PassArgs G{};
-    G.tile = c->tile;
-    G.ntiles = (c->K + c->tile - 1) / c->tile;
+    vamp::PassArgs G = pass_args(c, 0);
     G.rec_bytes = rec;
     G.batch = B;
     G.chunk = chunk;
@@ -517,7 +402,7 @@ vamp_status vamp_generate(vamp_ctx* c, int64_t n_events, uint32_t gen_id, void* 
         G.field = 0x80000000u | (gen_id << 16) | b;
         unsigned char* outp = (unsigned char*)dev_records + written * rec;
         if (c->prof) VAMP_CK(c, cudaEventRecord(c->ev[0], c->stream));
-        VAMP_CK(c, vamp::launch_pass(c->prm, c->fp32, 1, G, grid, c->smem_gen, c->stream));
+        VAMP_CK(c, c->var->launch(c->prm, 1, G, grid, c->smem_gen, c->stream));
         if (c->prof) VAMP_CK(c, cudaEventRecord(c->ev[1], c->stream));
         VAMP_CK(c, vamp::launch_gen_finish(c->prm, G, n_events - written, outp, c->stream));
         st = read_head(c);
@@ -623,13 +508,14 @@ vamp_status vamp_eval_calls(vamp_ctx* c, int32_t mode, uint32_t field, uint32_t 
     void* buf = nullptr;
     const size_t bytes = nx * 8 * 2 + nx * 4 + nb * 4 + (size_t)count * 4 * 8 + 1024;
     if (cudaMalloc(&buf, bytes) != cudaSuccess) return fail(c, VAMP_ERR_OOM, "eval buffer allocation failed");
+    auto a256 = [](size_t v) { return (v + 255) & ~size_t(255); };
     char* q = (char*)buf;
     vamp::EvalArgs A{};
     A.mode = mode; A.field = field; A.call0 = call0; A.count = count;
-    A.x = (double*)q; q += align256(nx * 8);
-    A.p = (double*)q; q += align256(nx * 8);
-    A.jf = (int*)q; q += align256(nx * 4);
-    A.fgwc = (double*)q; q += align256((size_t)count * 32);
+    A.x = (double*)q; q += a256(nx * 8);
+    A.p = (double*)q; q += a256(nx * 8);
+    A.jf = (int*)q; q += a256(nx * 4);
+    A.fgwc = (double*)q; q += a256((size_t)count * 32);
     A.bins = (int*)q;
     vamp_status st = VAMP_OK;
     cudaError_t e = vamp::launch_eval(c->prm, c->fp32, A, c->stream);

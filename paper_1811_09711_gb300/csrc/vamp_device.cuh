@@ -9,10 +9,11 @@
 //
 // Grid data of one channel lives in one contiguous "lookup block" so that a
 // tile of channels can be staged into shared memory with one bulk copy:
-//   [edges  d rows x Es][densities d rows x Dn][cell tables d rows x Ts bytes][span d bytes]
+//   [header: map constants of the channel]
+//   [row 0: edges (Es) | densities 1/(nΔx) (Dn) | cell table (Ts bytes)] [row 1] ...
 // The cell table of a row splits [0,1) into L = 2^lshift equal cells and
-// stores for cell q the bin containing q/L; a lookup then searches only the
-// bins between two table entries (span = the widest such range of the row).
+// stores for cell q the bin containing q/L (byte L+1 holds the row's span:
+// the most bins any cell overlaps), so a lookup starts next to its answer.
 #pragma once
 
 #include <cstdint>
@@ -27,7 +28,8 @@ constexpr int MAX_BINS = 256; // largest supported bins per axis (table entries 
 enum : int { MAP_ID = 0, MAP_BW = 1, MAP_POW = 2 };
 enum : unsigned { ERR_NONFINITE = 1u, ERR_TIMEOUT = 2u };
 
-// One channel map or one integrand peak, with derived constants.
+// Map constants of one channel or peak (used from global memory by the
+// non-matching integrand path and by the host).
 template <typename T>
 struct MapRec {
     int32_t nmap;
@@ -46,15 +48,28 @@ struct MapRec {
     T wz;               // peak weight x Z^-(d - nmap) (Gaussian normalisation)
 };
 
+// Slot constants inside a lookup-block header.
+enum : int { SP_M = 0, SP_G, SP_A, SP_G2, SP_INVG, SP_GINVA, SP_INVA, SP_T0, SP_DEL, SP_INVPOWN, SP_N };
+
+// Header of a lookup block: what the channel loop needs about channel c'.
+template <typename T>
+struct ChanHdr {
+    uint32_t mask;       // bit k: coordinate k is mapped
+    uint32_t kinds;      // byte s: map kind of slot s
+    uint64_t slotpack;   // 4 bits per coordinate: its slot
+    T wz;                // matching peak: weight x Z^-(d - nmap)
+    T pad[16 / sizeof(T) - 1];
+    T sp[MAXMAP][SP_N];  // per slot: m, Γ, A, Γ², 1/Γ, Γ/A, 1/A, atan(m/Γ), δ, 1/powN
+};
+
 // Byte layout of one channel's lookup block for element type T.
 struct BlkLayout {
+    int H;         // header bytes
     int Es;        // edges per row (>= n+1, padded)
     int Dn;        // densities per row (>= n, padded)
-    int Ts;        // table bytes per row (>= L+1, padded)
+    int Ts;        // table bytes per row (>= L+2, padded)
+    int R;         // row stride in bytes
     int lshift;    // L = 2^lshift cells per row
-    int off_dens;  // byte offsets inside the block
-    int off_tab;
-    int off_span;
     int bytes;     // block size (multiple of 16)
 };
 
@@ -89,9 +104,7 @@ struct Params {
     int64_t n_min;
     double grid_alpha, beta;
     int smooth, omega_mode;
-    // maps
-    const MapRec<double>* ch64;
-    const MapRec<float>* ch32;
+    // maps (host order, for the non-matching integrand)
     const MapRec<double>* pk64;
     const MapRec<float>* pk32;
     // Gaussian factor in log2 units: a_k = (p_k - centre)^2 * gk2
@@ -163,7 +176,6 @@ template <typename T> struct Prec;
 template <> struct Prec<double> {
     static __device__ __forceinline__ const unsigned char* lk(const Params& P) { return P.lk64; }
     static __device__ __forceinline__ const BlkLayout& lay(const Params& P) { return P.lay64; }
-    static __device__ __forceinline__ const MapRec<double>* ch(const Params& P) { return P.ch64; }
     static __device__ __forceinline__ const MapRec<double>* pk(const Params& P) { return P.pk64; }
     static __device__ __forceinline__ double alpha(const Params& P, int c) { return P.alpha[c]; }
     static __device__ __forceinline__ double gcen(const Params& P) { return P.gcen; }
@@ -198,7 +210,6 @@ template <> struct Prec<double> {
 template <> struct Prec<float> {
     static __device__ __forceinline__ const unsigned char* lk(const Params& P) { return P.lk32; }
     static __device__ __forceinline__ const BlkLayout& lay(const Params& P) { return P.lay32; }
-    static __device__ __forceinline__ const MapRec<float>* ch(const Params& P) { return P.ch32; }
     static __device__ __forceinline__ const MapRec<float>* pk(const Params& P) { return P.pk32; }
     static __device__ __forceinline__ float alpha(const Params& P, int c) { return P.alpha32[c]; }
     static __device__ __forceinline__ float gcen(const Params& P) { return P.gcen_f; }
@@ -221,89 +232,115 @@ template <> struct Prec<float> {
     }
 };
 
-__device__ __forceinline__ int slot_of(uint64_t slotpack, int k) { return (int)((slotpack >> (4 * k)) & 0xFu); }
+// ---------------------------------------------------------------------------
+// Shape policy: D_, NB_ > 0 fix the dimension and the bins at compile time
+// (all block offsets become constants); 0 means "read from the layout".
+// ---------------------------------------------------------------------------
+constexpr int ceil_log2(int v) { return v <= 1 ? 0 : 1 + ceil_log2((v + 1) / 2); }
+constexpr int round_up(int v, int m) { return (v + m - 1) / m * m; }
 
-// Views into a channel lookup block (global or shared memory).
 template <typename T>
-struct Blk {
-    const unsigned char* b;
-    __device__ __forceinline__ const T* e(const BlkLayout& L, int k) const
+__host__ __device__ constexpr BlkLayout make_layout_c(int d, int n)
+{
+    const int per16 = 16 / (int)sizeof(T);
+    const int es = round_up(n + 1, per16), dn = round_up(n, per16);
+    const int ls = ceil_log2(n) + 1 < 2 ? 2 : ceil_log2(n) + 1;
+    const int ts = round_up((1 << ls) + 2, 16);
+    const int h = (int)sizeof(ChanHdr<T>);
+    const int r = (es + dn) * (int)sizeof(T) + ts;
+    return BlkLayout{h, es, dn, ts, r, ls, h + d * r};
+}
+
+template <typename T, int D_, int NB_>
+struct Shape {
+    static constexpr bool kD = D_ > 0, kN = NB_ > 0;
+    static constexpr int DM = kD ? D_ : DMAX;  // unrolled loop bound
+    static constexpr BlkLayout C = make_layout_c<T>(kD ? D_ : 1, kN ? NB_ : 1);
+    const BlkLayout L;
+    const int d_rt, n_rt;
+    __device__ __forceinline__ Shape(const BlkLayout& l, int d, int n) : L(l), d_rt(d), n_rt(n) {}
+    __device__ __forceinline__ int d() const { return kD ? D_ : d_rt; }
+    __device__ __forceinline__ int n() const { return kN ? NB_ : n_rt; }
+    __device__ __forceinline__ int H() const { return kN ? C.H : L.H; }
+    __device__ __forceinline__ int R() const { return kN ? C.R : L.R; }
+    __device__ __forceinline__ int dens_off() const { return kN ? C.Es * (int)sizeof(T) : L.Es * (int)sizeof(T); }
+    __device__ __forceinline__ int tab_off() const { return kN ? (C.Es + C.Dn) * (int)sizeof(T) : (L.Es + L.Dn) * (int)sizeof(T); }
+    __device__ __forceinline__ int lshift() const { return kN ? C.lshift : L.lshift; }
+    __device__ __forceinline__ int bytes() const { return kN && kD ? C.bytes : L.bytes; }
+    __device__ __forceinline__ const unsigned char* row(const unsigned char* blk, int k) const
     {
-        return reinterpret_cast<const T*>(b) + k * L.Es;
+        return blk + H() + k * R();
     }
-    __device__ __forceinline__ const T* dn(const BlkLayout& L, int k) const
-    {
-        return reinterpret_cast<const T*>(b + L.off_dens) + k * L.Dn;
-    }
-    __device__ __forceinline__ const unsigned char* tb(const BlkLayout& L, int k) const
-    {
-        return b + L.off_tab + k * L.Ts;
-    }
-    __device__ __forceinline__ int span(const BlkLayout& L, int k) const { return b[L.off_span + k]; }
 };
 
-// Largest j in [0, n-1] with e[j] <= x (the oracle's bin rule), searching
-// only between the table entries of x's cell.
-template <typename T>
-__device__ __forceinline__ int lookup(const T* e, const unsigned char* tb, int span, int lshift, T x)
+// Largest j in [0, n-1] with e[j] <= x (the oracle's bin rule), starting at
+// the table entry of x's cell; no step passes the last bin of the row.
+template <typename T, class SH>
+__device__ __forceinline__ int lookup(const SH& sh, const unsigned char* row, int span, T x)
 {
-    const int q = Prec<T>::cell(x, lshift);
-    int j = tb[q];
-    const int hi = tb[q + 1];
+    const T* e = reinterpret_cast<const T*>(row);
+    const int q = Prec<T>::cell(x, sh.lshift());
+    int j = row[sh.tab_off() + q];
+    const int nm1 = sh.n() - 1;
     if (span <= 1) {
-        if (j < hi && Prec<T>::le(e[j + 1], x)) j += 1;
+        if (j < nm1 && Prec<T>::le(e[j + 1], x)) j += 1;
     } else {
         for (int s = 1 << (31 - __clz(span)); s > 0; s >>= 1) {
             const int t = j + s;
-            if (t <= hi && Prec<T>::le(e[t], x)) j = t;
+            if (t <= nm1 && Prec<T>::le(e[t], x)) j = t;
         }
     }
     return j;
 }
 
 // ---------------------------------------------------------------------------
-// Forward map of the selected channel: r -> x_c -> p, g_c(x_c) / φ'_c(x_c),
-// and the Gaussian exponent sum of p (log2 units).
+// Forward map of the selected channel (lookup block in global memory):
+// r -> x_c -> p, the own term g_c(x_c)/φ'_c(x_c) and the Gaussian exponent
+// sum of p (log2 units).
 // ---------------------------------------------------------------------------
-template <typename T>
-__device__ __forceinline__ void forward_call(const Params& P, int c, const uint32_t* X, T (&x)[DMAX],
-                                             T (&p)[DMAX], int (&jf)[DMAX], T& own_gJ, T& asum_all)
+template <typename T, class SH>
+__device__ __forceinline__ void forward_call(const Params& P, const SH& sh, int c, const uint32_t* X,
+                                             T (&x)[SH::DM], T (&p)[SH::DM], int (&jf)[SH::DM], T& own_gJ,
+                                             T& asum_all)
 {
-    const int d = P.d, n = P.n;
-    const BlkLayout& L = Prec<T>::lay(P);
-    const Blk<T> blk{Prec<T>::lk(P) + (size_t)c * L.bytes};
+    const int d = sh.d(), n = sh.n();
+    const unsigned char* blk = Prec<T>::lk(P) + (size_t)c * sh.bytes();
     T g = T(1);
 #pragma unroll
-    for (int k = 0; k < DMAX; ++k) {
+    for (int k = 0; k < SH::DM; ++k) {
         if (k < d) {
             const uint64_t t = (2ull * X[k] + 1ull) * (uint64_t)n;
             const int j = (int)(t >> 33);
             const T fr = Prec<T>::frac(t & ((1ull << 33) - 1ull));
-            const T* e = blk.e(L, k);
+            const unsigned char* row = sh.row(blk, k);
+            const T* e = reinterpret_cast<const T*>(row);
             x[k] = Prec<T>::lerp(__ldg(e + j), __ldg(e + j + 1), fr);
             jf[k] = j;
-            g *= __ldg(blk.dn(L, k) + j);
+            g *= __ldg(reinterpret_cast<const T*>(row + sh.dens_off()) + j);
         } else {
             x[k] = T(0);
             jf[k] = 0;
         }
     }
-    const MapRec<T>& r = Prec<T>::ch(P)[c];
-    const uint32_t mask = r.mask;
+    const ChanHdr<T>* h = reinterpret_cast<const ChanHdr<T>*>(blk);
+    const uint32_t mask = __ldg(&h->mask), kinds = __ldg(&h->kinds);
+    const uint64_t slotpack = __ldg(&h->slotpack);
     T J = T(1), A = T(0);
     const T gc = Prec<T>::gcen(P), k2 = Prec<T>::gk2(P);
 #pragma unroll
-    for (int k = 0; k < DMAX; ++k) {
+    for (int k = 0; k < SH::DM; ++k) {
         p[k] = x[k];
         if (k < d) {
             if ((mask >> k) & 1u) {
-                const int s = slot_of(r.slotpack, k);
-                if (r.kind[s] == MAP_BW) {
-                    const T mass = r.m[s], G = r.G[s];
-                    p[k] = mass + G * Prec<T>::tan_(r.A[s] * x[k] - r.t0[s]);
+                const int s = (int)((slotpack >> (4 * k)) & 0xFu);
+                const int kind = (kinds >> (8 * s)) & 0xff;
+                const T* sp = h->sp[s];
+                if (kind == MAP_BW) {
+                    const T mass = __ldg(sp + SP_M), G = __ldg(sp + SP_G), A_ = __ldg(sp + SP_A);
+                    p[k] = mass + G * Prec<T>::tan_(A_ * x[k] - __ldg(sp + SP_T0));
                     const T dp = p[k] - mass;
-                    J *= r.GinvA[s] / (dp * dp + G * G);
-                } else if (r.kind[s] == MAP_POW) {
+                    J *= __ldg(sp + SP_GINVA) / (dp * dp + __ldg(sp + SP_G2));
+                } else if (kind == MAP_POW) {
                     const T x2 = x[k] * x[k], x4 = x2 * x2;
                     T pk = x4 * x[k];
                     if (pk < Prec<T>::tiny()) pk = Prec<T>::tiny();
@@ -320,48 +357,51 @@ __device__ __forceinline__ void forward_call(const Params& P, int c, const uint3
 }
 
 // ---------------------------------------------------------------------------
-// One channel c' against CPT calls (the inner loop of Eq. 30, fused with
-// the matching integrand peak when `with_f`):
-//   g_q += α_c' g_c'(φ_c'^{-1}(p_q)) / φ'_c'   (unless skip_q)
+// One channel c' (block in shared or global memory) against CPT calls: the
+// inner loop of Eq. 30, fused with the matching integrand peak when with_f:
+//   g_q += α_c' g_c'(φ_c'^{-1}(p_q)) / φ'_c'   (lookups and not skip_q)
 //   f_q += wz_c' 2^-(A_q - Σ_mapped a_k) Π_mapped factor(p_k)
 // REC records the bin indices of call 0 into bins[0..d-1].
 // ---------------------------------------------------------------------------
-template <typename T, int CPT, bool REC>
-__device__ __forceinline__ void channel_body(const Params& P, const MapRec<T>& r, const Blk<T>& blk, T alpha_c,
-                                             bool lookups, bool with_f, const T (&p)[CPT][DMAX],
+template <typename T, int CPT, bool REC, class SH>
+__device__ __forceinline__ void channel_body(const Params& P, const SH& sh, const unsigned char* blk, T alpha_c,
+                                             bool lookups, bool with_f, const T (&p)[CPT][SH::DM],
                                              const T (&A)[CPT], const bool (&skip)[CPT], T (&g)[CPT],
                                              T (&f)[CPT], int* bins)
 {
-    const int d = P.d;
-    const BlkLayout& L = Prec<T>::lay(P);
-    const uint32_t mask = r.mask;
+    const int d = sh.d();
+    const ChanHdr<T>& h = *reinterpret_cast<const ChanHdr<T>*>(blk);
+    const uint32_t mask = h.mask, kinds = h.kinds;
+    const uint64_t slotpack = h.slotpack;
     const T gc = Prec<T>::gcen(P), k2 = Prec<T>::gk2(P);
     T J[CPT], F[CPT], gp[CPT], as[CPT];
 #pragma unroll
     for (int q = 0; q < CPT; ++q) { J[q] = T(1); F[q] = T(1); gp[q] = T(1); as[q] = T(0); }
 #pragma unroll
-    for (int k = 0; k < DMAX; ++k) {
+    for (int k = 0; k < SH::DM; ++k) {
         if (k < d) {
             T xk[CPT];
 #pragma unroll
             for (int q = 0; q < CPT; ++q) xk[q] = p[q][k];
             if ((mask >> k) & 1u) {
-                const int s = slot_of(r.slotpack, k);
-                if (r.kind[s] == MAP_BW) {
-                    const T mass = r.m[s], G = r.G[s], invG = r.invG[s], GinvA = r.GinvA[s], invA = r.invA[s],
-                            t0 = r.t0[s];
+                const int s = (int)((slotpack >> (4 * k)) & 0xFu);
+                const int kind = (kinds >> (8 * s)) & 0xff;
+                const T* sp = h.sp[s];
+                if (kind == MAP_BW) {
+                    const T mass = sp[SP_M], G2 = sp[SP_G2], invG = sp[SP_INVG], GinvA = sp[SP_GINVA],
+                            invA = sp[SP_INVA], t0 = sp[SP_T0];
 #pragma unroll
                     for (int q = 0; q < CPT; ++q) {
                         const T dp = p[q][k] - mass;
-                        const T jfac = GinvA / (dp * dp + G * G);
+                        const T jfac = GinvA / (dp * dp + G2);
                         J[q] *= jfac;
                         F[q] *= jfac;
                         xk[q] = (Prec<T>::atan_(dp * invG) + t0) * invA;
                         const T u = p[q][k] - gc;
                         as[q] += u * u * k2;
                     }
-                } else if (r.kind[s] == MAP_POW) {
-                    const T del = r.del[s], ipn = r.invPowN[s];
+                } else if (kind == MAP_POW) {
+                    const T del = sp[SP_DEL], ipn = sp[SP_INVPOWN];
 #pragma unroll
                     for (int q = 0; q < CPT; ++q) {
                         const T xx = Prec<T>::pow02(p[q][k]);
@@ -375,31 +415,30 @@ __device__ __forceinline__ void channel_body(const Params& P, const MapRec<T>& r
                 }
             }
             if (lookups) {
-                const T* e = blk.e(L, k);
-                const T* dn = blk.dn(L, k);
-                const unsigned char* tb = blk.tb(L, k);
-                const int sp = blk.span(L, k);
+                const unsigned char* row = sh.row(blk, k);
+                const T* dn = reinterpret_cast<const T*>(row + sh.dens_off());
+                const int sp = row[sh.tab_off() + (1 << sh.lshift()) + 1];
 #pragma unroll
                 for (int q = 0; q < CPT; ++q) {
-                    const int j = lookup<T>(e, tb, sp, L.lshift, xk[q]);
+                    const int j = lookup<T>(sh, row, sp, xk[q]);
                     if (REC && q == 0) bins[k] = j;
                     gp[q] *= dn[j];
                 }
             }
         }
     }
+    const T wz = h.wz;
 #pragma unroll
     for (int q = 0; q < CPT; ++q) {
         if (lookups && !skip[q]) g[q] += alpha_c * gp[q] * J[q];
-        if (with_f) f[q] += r.wz * Prec<T>::exp2_(as[q] - A[q]) * F[q];
+        if (with_f) f[q] += wz * Prec<T>::exp2_(as[q] - A[q]) * F[q];
     }
 }
 
 // Integrand of a non-matching problem: loop over its own peaks.
-template <typename T>
-__device__ __forceinline__ T integrand_peaks(const Params& P, const T (&p)[DMAX], T A)
+template <typename T, int DM>
+__device__ __forceinline__ T integrand_peaks(const Params& P, int d, const T (&p)[DM], T A)
 {
-    const int d = P.d;
     const MapRec<T>* pks = Prec<T>::pk(P);
     const T gc = Prec<T>::gcen(P), k2 = Prec<T>::gk2(P);
     T f = T(0);
@@ -408,9 +447,9 @@ __device__ __forceinline__ T integrand_peaks(const Params& P, const T (&p)[DMAX]
         const uint32_t mask = r.mask;
         T v = T(1), as = T(0);
 #pragma unroll
-        for (int k = 0; k < DMAX; ++k) {
+        for (int k = 0; k < DM; ++k) {
             if (k < d && ((mask >> k) & 1u)) {
-                const int s = slot_of(r.slotpack, k);
+                const int s = (int)((r.slotpack >> (4 * k)) & 0xFu);
                 if (r.kind[s] == MAP_BW) {
                     const T dp = p[k] - r.m[s];
                     v *= r.GinvA[s] / (dp * dp + r.G[s] * r.G[s]);
@@ -438,6 +477,16 @@ __device__ __forceinline__ int choose_channel(const Params& P, double u)
     if (!(tgt < P.Acum[lo])) { // rounding: last live channel
         for (int c = P.K - 1; c >= 0; --c)
             if (P.alpha[c] > 0.0) return c;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int find_channel(const int64_t* Pc, int K, int64_t i)
+{
+    int lo = 0, hi = K - 1; // largest c with Pc[c] <= i
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (Pc[mid] <= i) lo = mid; else hi = mid - 1;
     }
     return lo;
 }

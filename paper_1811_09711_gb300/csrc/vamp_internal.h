@@ -1,19 +1,24 @@
-// vamp_internal.h -- launch interface between the C ABI (vamp_api.cu) and
-// the kernels (vamp_kernels.cu).  Not part of the public ABI.
+// vamp_internal.h -- interface between the C ABI (vamp_api.cu,
+// vamp_noalloc.cu), the host-side setup (vamp_setup.cu) and the kernels.
+// Not part of the public ABI.
 #pragma once
 
 #include <cstdint>
+#include <string>
+#include <vector>
 #include <cuda_runtime.h>
+
+#include "../../include/vamp.h"
 
 namespace vamp {
 
 struct Params;
+template <typename T> struct MapRec;
 
 constexpr int PASS_THREADS = 256;  // threads per pass CTA
-constexpr int CPT32 = 2;           // calls per thread, FP32-eval pass
-constexpr int CPT64 = 1;           // calls per thread, FP64 pass
 constexpr int SMEM_HEAD = 512;     // bytes of barriers and scratch before the tile buffers
 constexpr int REFINE_WARPS = 4;    // grid rows per refine CTA
+constexpr size_t TILE_BUDGET = 112 * 1024;  // pass-kernel shared memory per CTA (two CTAs per SM)
 
 // Launch arguments of the pass kernel.  Integration: `field` = iteration.
 // Generation: calls [0, batch) of stream `field`, in chunks of `chunk` =
@@ -45,10 +50,48 @@ struct EvalArgs {
     double* fgwc;
 };
 
+// One compiled pass kernel pair (integration, generation): precision, calls
+// per thread, and the shape it is specialised for (D = NB = 0: any shape).
+struct PassVariant {
+    int fp32, cpt, D, NB;
+    const void* fn[2];
+    cudaError_t (*launch)(const Params& P, int mode, const PassArgs& A, int grid, size_t smem, cudaStream_t s);
+};
+
+void add_pass_variants_f32_generic(std::vector<PassVariant>& v);
+void add_pass_variants_f32_shapes(std::vector<PassVariant>& v);
+void add_pass_variants_f64(std::vector<PassVariant>& v);
+
+// Host-side data derived from a vamp_config (vamp_setup.cu).
+struct Setup {
+    int d = 0, K = 0, n = 0, P = 0, fp32 = 0;
+    double zinv = 1.0;
+    std::vector<unsigned char> hdr64, hdr32;  // K lookup-block headers each
+    std::vector<unsigned char> pk64, pk32;    // P MapRec records each (non-matching integrand)
+};
+
+// Validates cfg, fills the scalar fields of P (keys, layouts, Gaussian,
+// matching flag) and the host images in S.  Returns false with a reason.
+bool build_setup(const vamp_config* cfg, Params& P, Setup& S, std::string& why);
+
+// Device-side placement of the per-problem arrays inside one buffer.
+struct Arena {
+    size_t edges64, lk64, lk32, alpha, alpha32, shift, acum, nc, pc, D, csum, ic, vc, wc, pk64, pk32, sc;
+    size_t bytes;
+};
+Arena plan_arena(const Params& P);
+void bind_arena(Params& P, unsigned char* base, const Arena& A);  // sets every array pointer
+// Copies headers and peak records into the arena (async on s).
+cudaError_t upload_setup(const Params& P, const Setup& S, cudaStream_t s);
+
+// Tile and shared-memory size of the pass kernel for element size esz.
+void pass_smem(const Params& P, int fp32, int* tile, size_t* smem_int, size_t* smem_gen);
+// Candidate kernels for a shape: exact (D, NB) matches first, then generic.
+std::vector<const PassVariant*> pass_candidates(int fp32, int d, int n);
+// Raises (never lowers) the dynamic shared-memory limit of a kernel.
+cudaError_t ensure_smem(const void* fn, size_t bytes);
+
 cudaError_t launch_begin_pass(const Params& P, int64_t N, cudaStream_t s);
-const void* pass_kernel(int fp32, int mode);
-cudaError_t launch_pass(const Params& P, int fp32, int mode, const PassArgs& A, int grid, size_t smem,
-                        cudaStream_t s);
 cudaError_t launch_finish_pass(const Params& P, int combine, cudaStream_t s);
 cudaError_t launch_derive(const Params& P, cudaStream_t s);
 cudaError_t launch_refine(const Params& P, cudaStream_t s);

@@ -1,41 +1,16 @@
-// vamp_kernels.cu -- CUDA kernels of the multi-channel integrator's hot path.
+// vamp_kernels.cu -- the small kernels around the pass kernel (vamp_pass.cuh):
 //
 //   k_begin_pass      integer call allocation N_c, prefix P_c (§3.4)
-//   k_pass<T,0,CPT>   the sampling pass (§3.5 work order; Eqs. 15, 30, 31)
-//   k_pass<T,1,CPT>   one generation batch: α-random channel, accept
-//                     u w_max < w, ordered compaction (§2 Eq. 2, §3.5)
 //   k_finish_pass     per-channel means/variances, pass result, combination
 //   k_refine          VEGAS rebinning of every (channel, axis) row (Eqs. 14, 15)
 //   k_update_alpha    channel-weight update (Eq. 25)
-//   k_derive          lookup blocks: densities 1/(n Δx), cell tables, FP32 copies
-//   k_gen_scan / k_gen_copy / k_gen_end   ordered output of a generation batch
+//   k_derive          lookup-block rows: densities 1/(n Δx), cell tables, FP32 copies
+//   k_gen_prepare / k_gen_scan / k_gen_copy / k_gen_end   generation bookkeeping
 //   k_eval<T>         per-call diagnostics for parity tests
-//
-// The pass kernel is persistent: each CTA owns a contiguous range of calls
-// (integration) or a strided set of call chunks (generation), processed in
-// batches of THREADS*CPT calls.  Per batch it streams the lookup blocks of
-// all channels through shared memory in tiles, double-buffered with
-// cp.async.bulk copies completing on mbarriers; every wait is bounded.
 #include "vamp_device.cuh"
 #include "vamp_internal.h"
 
 namespace vamp {
-
-// ---------------------------------------------------------------------------
-// reductions
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ double warp_sum(double v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-__device__ __forceinline__ double warp_max(double v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
-}
 
 // ---------------------------------------------------------------------------
 // allocation (R6: N_c = max(N_min, floor(α_c N)) for α_c > 0)
@@ -58,298 +33,6 @@ __global__ void k_begin_pass(Params P, int64_t N)
         P.sc->n_total = acc;
         P.sc->wmax_bits = 0ull;
     }
-}
-
-__device__ __forceinline__ int find_channel(const int64_t* Pc, int K, int64_t i)
-{
-    int lo = 0, hi = K - 1; // largest c with Pc[c] <= i
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (Pc[mid] <= i) lo = mid; else hi = mid - 1;
-    }
-    return lo;
-}
-
-// ---------------------------------------------------------------------------
-// the pass kernel
-// ---------------------------------------------------------------------------
-struct SmemHead {
-    uint64_t bar[2];
-    int abort;
-    int pad;
-    double red[3][PASS_THREADS / 32];
-    int wcnt[PASS_THREADS / 32];
-    int woff[PASS_THREADS / 32];
-    int round_total;
-};
-
-template <typename T, int MODE, int CPT>
-__global__ void __launch_bounds__(PASS_THREADS, 2) k_pass(Params P, PassArgs A)
-{
-    extern __shared__ __align__(128) unsigned char smem[];
-    SmemHead& H = *reinterpret_cast<SmemHead*>(smem);
-    unsigned char* buf0 = smem + SMEM_HEAD;
-    const BlkLayout& L = Prec<T>::lay(P);
-    const int S = L.bytes;
-    const size_t tile_bytes = (size_t)A.tile * S;
-    double* Ds = reinterpret_cast<double*>(buf0 + (size_t)2 * A.tile * S);
-    const int d = P.d, n = P.n, dn = d * n, K = P.K;
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    constexpr int B = PASS_THREADS * CPT;
-    const unsigned char* lk = Prec<T>::lk(P);
-
-    // ---- work of this CTA ---------------------------------------------------
-    int64_t r0 = 0, r1 = 0;
-    int64_t nbatch = 0;
-    if (MODE == 0) {
-        const int64_t N = P.sc->n_total;
-        r0 = N * blockIdx.x / gridDim.x;
-        r1 = N * (blockIdx.x + 1) / gridDim.x;
-        int64_t i = r0;
-        while (i < r1) {
-            const int c = find_channel(P.Pc, K, i);
-            const int64_t e = min(r1, P.Pc[c + 1]);
-            nbatch += (e - i + B - 1) / B;
-            i = e;
-        }
-    } else {
-        const int64_t nch = A.nchunks;
-        nbatch = blockIdx.x < nch ? (nch - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-    }
-    if (nbatch == 0) return;
-    const int ntiles = A.ntiles;
-    const bool streaming = ntiles > 2;
-    const int64_t total_uses = streaming ? nbatch * ntiles : ntiles;
-
-    auto issue = [&](int64_t u) {
-        const int t = (int)(u % ntiles);
-        const int cnt = min(A.tile, K - t * A.tile);
-        fence_proxy_async_smem();
-        bulk_load(buf0 + (u & 1) * tile_bytes, lk + (size_t)t * tile_bytes, (uint32_t)(cnt * S), &H.bar[u & 1]);
-    };
-    if (tid == 0) {
-        mbar_init(&H.bar[0], 1);
-        mbar_init(&H.bar[1], 1);
-        H.abort = 0;
-        fence_mbar_init();
-    }
-    __syncthreads();
-    if (tid == 0) {
-        issue(0);
-        if (total_uses > 1) issue(1);
-    }
-    int64_t u = 0;              // next tile use to consume
-    int64_t issued = total_uses > 1 ? 2 : 1;
-    double wm = 0.0, s1 = 0.0, s2 = 0.0;
-    bool bad = false;
-
-    // integration segment state
-    int64_t i0 = r0;
-    int cseg = -1;
-    int64_t seg_end = 0;
-    double sft = 0.0;
-    // generation chunk state
-    int64_t chunk = blockIdx.x;
-
-    for (int64_t bt = 0; bt < nbatch; ++bt) {
-        int64_t base, end;
-        if (MODE == 0) {
-            if (i0 >= seg_end || cseg < 0) {
-                // new segment of one channel: reset the shared d-values
-                cseg = find_channel(P.Pc, K, i0);
-                seg_end = min(r1, P.Pc[cseg + 1]);
-                sft = P.shift[cseg];
-                for (int q = tid; q < dn; q += PASS_THREADS) Ds[q] = 0.0;
-                s1 = s2 = 0.0;
-                __syncthreads();
-            }
-            base = i0;
-            end = min(seg_end, i0 + B);
-        } else {
-            base = chunk * B;
-            end = min(A.batch, base + B);
-        }
-
-        // ---- phase A: own channel forward map, integrand --------------------
-        T p[CPT][DMAX], g[CPT], f[CPT], Aexp[CPT];
-        bool skip[CPT], valid[CPT];
-        int cq[CPT];
-        uint32_t jp[CPT][4];
-        uint32_t xacc[CPT];
-#pragma unroll
-        for (int q = 0; q < CPT; ++q) {
-            const int64_t i = base + (int64_t)q * PASS_THREADS + tid;
-            valid[q] = i < end;
-            uint32_t X[DMAX + 4];
-            call_words<DMAX + 4>(P, (uint32_t)(valid[q] ? i : base), A.field, MODE == 0 ? d : d + 2, X);
-            int c;
-            if (MODE == 0) {
-                c = cseg;
-                xacc[q] = 0u;
-            } else {
-                uint32_t xc = 0u, xa = 0u;
-#pragma unroll
-                for (int k = 0; k < DMAX + 4; ++k) {
-                    if (k == d) xc = X[k];
-                    if (k == d + 1) xa = X[k];
-                }
-                c = choose_channel(P, unif64(xc));
-                xacc[q] = xa;
-            }
-            cq[q] = c;
-            T x[DMAX];
-            int jf[DMAX];
-            T owngJ, Aq;
-            forward_call<T>(P, c, X, x, p[q], jf, owngJ, Aq);
-            Aexp[q] = Aq;
-#pragma unroll
-            for (int w = 0; w < 4; ++w) {
-                uint32_t v = 0;
-#pragma unroll
-                for (int b = 0; b < 4; ++b) v |= (uint32_t)(jf[4 * w + b] & 0xff) << (8 * b);
-                jp[q][w] = v;
-            }
-            g[q] = Prec<T>::alpha(P, c) * owngJ;
-            f[q] = P.matching ? T(0) : integrand_peaks<T>(P, p[q], Aq);
-        }
-
-        // ---- phase B: every channel's term of g(p) (and the matching peaks) --
-        for (int t = 0; t < ntiles; ++t) {
-            // streaming: use u lives in buffer u%2 (phase u/2); otherwise tile t
-            // stays in buffer t after the first batch
-            const int b = streaming ? (int)(u & 1) : t;
-            if (streaming || bt == 0) {
-                if (!mbar_wait_bounded(&H.bar[b], streaming ? (uint32_t)((u >> 1) & 1) : 0u)) {
-                    atomicOr(&P.sc->err, ERR_TIMEOUT);
-                    H.abort = 1;
-                }
-            }
-            if (!H.abort) {
-                const int cnt = min(A.tile, K - t * A.tile);
-                for (int cl = 0; cl < cnt; ++cl) {
-                    const int c2 = t * A.tile + cl;
-                    const MapRec<T>& r = Prec<T>::ch(P)[c2];
-                    const T a = Prec<T>::alpha(P, c2);
-                    const bool lookups = (a != T(0)) && !(MODE == 0 && c2 == cseg);
-#pragma unroll
-                    for (int q = 0; q < CPT; ++q) skip[q] = (MODE == 1) && (cq[q] == c2);
-                    const Blk<T> blk{buf0 + b * tile_bytes + (size_t)cl * S};
-                    channel_body<T, CPT, false>(P, r, blk, a, lookups, P.matching != 0, p, Aexp, skip, g, f,
-                                                nullptr);
-                }
-            }
-            __syncthreads();
-            if (H.abort) goto drain;
-            if (streaming && tid == 0 && issued < total_uses) {
-                issue(issued);
-                ++issued;
-            }
-            ++u;
-        }
-
-        // ---- phase C: weights and accumulation ------------------------------
-        if (MODE == 0) {
-#pragma unroll
-            for (int q = 0; q < CPT; ++q) {
-                if (!valid[q]) continue;
-                double w = g[q] > T(0) ? (double)(f[q] / g[q]) : 0.0;
-                if (!isfinite(w)) { bad = true; w = 0.0; }
-                const double dv = w - sft;
-                s1 += dv;
-                s2 += dv * dv;
-                wm = fmax(wm, w);
-                const double w2 = w * w;
-#pragma unroll
-                for (int k = 0; k < DMAX; ++k)
-                    if (k < d) atomicAdd(&Ds[k * n + ((jp[q][k >> 2] >> (8 * (k & 3))) & 0xff)], w2);
-            }
-            i0 = end;
-            if (i0 >= seg_end) {
-                // end of the segment: flush its sums and d-values
-                s1 = warp_sum(s1);
-                s2 = warp_sum(s2);
-                if (lane == 0) { H.red[0][wid] = s1; H.red[1][wid] = s2; }
-                __syncthreads();
-                if (tid == 0) {
-                    double a = 0.0, bb = 0.0;
-                    for (int q = 0; q < PASS_THREADS / 32; ++q) { a += H.red[0][q]; bb += H.red[1][q]; }
-                    atomicAdd(&P.csum[2 * cseg], a);
-                    atomicAdd(&P.csum[2 * cseg + 1], bb);
-                }
-                double* Dg = P.D + (size_t)cseg * dn;
-                for (int q = tid; q < dn; q += PASS_THREADS) {
-                    const double v = Ds[q];
-                    if (v != 0.0) atomicAdd(&Dg[q], v);
-                }
-                s1 = s2 = 0.0;
-                __syncthreads();
-            }
-        } else {
-            const double wmax = P.sc->wmax_gen;
-            int running = 0;
-            const int64_t cbase = chunk * B;
-#pragma unroll
-            for (int q = 0; q < CPT; ++q) {
-                double w = 0.0;
-                bool acc = false;
-                if (valid[q]) {
-                    w = g[q] > T(0) ? (double)(f[q] / g[q]) : 0.0;
-                    if (!isfinite(w)) { bad = true; w = 0.0; }
-                    wm = fmax(wm, w);
-                    acc = unif64(xacc[q]) * wmax < w;
-                }
-                const unsigned bal = __ballot_sync(0xffffffffu, acc);
-                if (lane == 0) H.wcnt[wid] = __popc(bal);
-                __syncthreads();
-                if (tid == 0) {
-                    int s = 0;
-                    for (int w2 = 0; w2 < PASS_THREADS / 32; ++w2) { H.woff[w2] = s; s += H.wcnt[w2]; }
-                    H.round_total = s;
-                }
-                __syncthreads();
-                if (acc) {
-                    const int pos = running + H.woff[wid] + __popc(bal & ((1u << lane) - 1u));
-                    const int64_t slot = cbase + pos;
-                    unsigned char* rec = A.staging + slot * A.rec_bytes;
-                    float* pf = reinterpret_cast<float*>(rec);
-#pragma unroll
-                    for (int k = 0; k < DMAX; ++k)
-                        if (k < d) pf[k] = (float)p[q][k];
-                    if (d & 1) pf[d] = 0.0f;
-                    *reinterpret_cast<double*>(rec + A.rec_bytes - 8) = w;
-                    A.callidx[slot] = (uint32_t)(base + (int64_t)q * PASS_THREADS + tid);
-                }
-                running += H.round_total;
-                __syncthreads();
-            }
-            if (tid == 0) A.counts[chunk] = running;
-            chunk += gridDim.x;
-        }
-    }
-
-    // ---- CTA totals --------------------------------------------------------
-    wm = warp_max(wm);
-    if (lane == 0) H.red[2][wid] = wm;
-    if (bad) atomicOr(&P.sc->err, ERR_NONFINITE);
-    __syncthreads();
-    if (tid == 0) {
-        double m = 0.0;
-        for (int q = 0; q < PASS_THREADS / 32; ++q) m = fmax(m, H.red[2][q]);
-        unsigned long long* dst = MODE == 0 ? &P.sc->wmax_bits : &P.sc->gen_bmax_bits;
-        atomicMax(dst, (unsigned long long)__double_as_longlong(m));
-    }
-    return;
-
-drain:
-    // a wait gave up: let this CTA's copies in flight land (bounded), then exit
-    if (tid == 0) {
-        if (streaming) {
-            for (int64_t v = u; v < issued; ++v) mbar_wait_bounded(&H.bar[v & 1], (uint32_t)((v >> 1) & 1));
-        } else {
-            for (int64_t v = u; v < issued; ++v) mbar_wait_bounded(&H.bar[v], 0u);
-        }
-    }
-    __syncthreads();
 }
 
 // ---------------------------------------------------------------------------
@@ -438,10 +121,10 @@ __device__ __forceinline__ void derive_row_t(const Params& P, const BlkLayout& L
     const int n = P.n, d = P.d;
     const int c = row / d, k = row % d;
     const double* e64 = P.edges64 + (size_t)row * (n + 1);
-    unsigned char* blk = lk + (size_t)c * L.bytes;
-    T* e = reinterpret_cast<T*>(blk) + k * L.Es;
-    T* dnr = reinterpret_cast<T*>(blk + L.off_dens) + k * L.Dn;
-    unsigned char* tb = blk + L.off_tab + k * L.Ts;
+    unsigned char* r = lk + (size_t)c * L.bytes + L.H + (size_t)k * L.R;
+    T* e = reinterpret_cast<T*>(r);
+    T* dnr = reinterpret_cast<T*>(r + L.Es * sizeof(T));
+    unsigned char* tb = r + (L.Es + L.Dn) * sizeof(T);
     for (int j = lane; j <= n; j += nl) {
         e[j] = (T)e64[j];
         if (j < n) dnr[j] = (T)(1.0 / ((double)n * (e64[j + 1] - e64[j])));
@@ -449,7 +132,6 @@ __device__ __forceinline__ void derive_row_t(const Params& P, const BlkLayout& L
     __syncwarp();
     // tb[q] = largest j in [0, n-1] with e[j] <= q/L, for q = 0..L
     const int Lc = 1 << L.lshift;
-    int span = 0;
     for (int q = lane; q <= Lc; q += nl) {
         const T xq = (T)q / (T)Lc;
         int lo = 0, hi = n - 1;
@@ -460,10 +142,11 @@ __device__ __forceinline__ void derive_row_t(const Params& P, const BlkLayout& L
         tb[q] = (unsigned char)lo;
     }
     __syncwarp();
+    int span = 0;
     for (int q = lane; q < Lc; q += nl) span = max(span, (int)tb[q + 1] - (int)tb[q]);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) span = max(span, __shfl_xor_sync(0xffffffffu, span, o));
-    if (lane == 0) blk[L.off_span + k] = (unsigned char)min(span, 255);
+    if (lane == 0) tb[Lc + 1] = (unsigned char)min(span, 255);
 }
 
 __device__ __forceinline__ void derive_row(const Params& P, int row, int lane)
@@ -675,8 +358,10 @@ __global__ void k_gen_end(Params P)
 template <typename T>
 __global__ void k_eval(Params P, EvalArgs A)
 {
+    using SH = Shape<T, 0, 0>;
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= A.count) return;
+    const SH sh(Prec<T>::lay(P), P.d, P.n);
     const int d = P.d;
     const uint32_t call = A.call0 + (uint32_t)q;
     uint32_t X[DMAX + 4];
@@ -695,18 +380,16 @@ __global__ void k_eval(Params P, EvalArgs A)
     bool skip[1];
     int jf[DMAX];
     T owngJ;
-    forward_call<T>(P, c, X, x, p1[0], jf, owngJ, Aq[0]);
+    forward_call<T>(P, sh, c, X, x, p1[0], jf, owngJ, Aq[0]);
     g[0] = Prec<T>::alpha(P, c) * owngJ;
-    f[0] = P.matching ? T(0) : integrand_peaks<T>(P, p1[0], Aq[0]);
-    const BlkLayout& L = Prec<T>::lay(P);
+    f[0] = P.matching ? T(0) : integrand_peaks<T, DMAX>(P, d, p1[0], Aq[0]);
     int* bins = A.bins + (size_t)q * P.K * d;
     for (int c2 = 0; c2 < P.K; ++c2) {
         const T a = Prec<T>::alpha(P, c2);
         const bool lookups = a != T(0) && c2 != c;
         skip[0] = false;
-        const Blk<T> blk{Prec<T>::lk(P) + (size_t)c2 * L.bytes};
-        channel_body<T, 1, true>(P, Prec<T>::ch(P)[c2], blk, a, lookups, P.matching != 0, p1, Aq, skip, g, f,
-                                 bins + c2 * d);
+        const unsigned char* blk = Prec<T>::lk(P) + (size_t)c2 * sh.bytes();
+        channel_body<T, 1, true>(P, sh, blk, a, lookups, P.matching != 0, p1, Aq, skip, g, f, bins + c2 * d);
         if (a == T(0))
             for (int k = 0; k < d; ++k) bins[c2 * d + k] = -1;
         else if (c2 == c)
@@ -730,31 +413,6 @@ __global__ void k_eval(Params P, EvalArgs A)
 cudaError_t launch_begin_pass(const Params& P, int64_t N, cudaStream_t s)
 {
     k_begin_pass<<<1, 32, 0, s>>>(P, N);
-    return cudaGetLastError();
-}
-
-template <typename T, int MODE>
-static const void* pass_fn()
-{
-    return (const void*)k_pass<T, MODE, (sizeof(T) == 4 ? CPT32 : CPT64)>;
-}
-
-const void* pass_kernel(int fp32, int mode)
-{
-    if (fp32) return mode ? pass_fn<float, 1>() : pass_fn<float, 0>();
-    return mode ? pass_fn<double, 1>() : pass_fn<double, 0>();
-}
-
-cudaError_t launch_pass(const Params& P, int fp32, int mode, const PassArgs& A, int grid, size_t smem,
-                        cudaStream_t s)
-{
-    if (fp32) {
-        if (mode) k_pass<float, 1, CPT32><<<grid, PASS_THREADS, smem, s>>>(P, A);
-        else k_pass<float, 0, CPT32><<<grid, PASS_THREADS, smem, s>>>(P, A);
-    } else {
-        if (mode) k_pass<double, 1, CPT64><<<grid, PASS_THREADS, smem, s>>>(P, A);
-        else k_pass<double, 0, CPT64><<<grid, PASS_THREADS, smem, s>>>(P, A);
-    }
     return cudaGetLastError();
 }
 

@@ -1,0 +1,343 @@
+// vamp_pass.cuh -- the persistent pass kernel, templated on precision, mode
+// (0 integration, 1 generation), calls per thread and problem shape.
+//
+// Each CTA owns a contiguous range of calls (integration: split further at
+// channel boundaries so that its d-value accumulators in shared memory
+// belong to one channel) or a strided set of call chunks (generation), and
+// processes them in batches of PASS_THREADS*CPT calls:
+//   A  per call: Philox words, channel (integration: the segment's; generation:
+//      drawn from α), forward map x_c -> p on the channel's grid, its own term
+//      α_c g_c/φ'_c of g(p), Gaussian exponent sum (and the integrand when the
+//      peaks are not the channels' maps);
+//   B  every channel's term of g(p) (Eq. 30) and the matching integrand peak,
+//      with the channels' lookup blocks streamed through shared memory in
+//      tiles (cp.async.bulk, two buffers, bounded mbarrier waits);
+//   C  w = f/g: per-channel shifted sums, d-values D_{c,k,j} += w² (Eq. 15),
+//      max weight (integration); accept u w_max < w and ordered compaction
+//      of the event records (generation).
+#pragma once
+
+#include "vamp_device.cuh"
+#include "vamp_internal.h"
+
+namespace vamp {
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_max(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+struct SmemHead {
+    uint64_t bar[2];
+    int abort;
+    int pad;
+    double red[3][PASS_THREADS / 32];
+    int wcnt[PASS_THREADS / 32];
+    int woff[PASS_THREADS / 32];
+    int round_total;
+};
+static_assert(sizeof(SmemHead) <= SMEM_HEAD, "shared-memory head too large");
+
+template <typename T, int MODE, int CPT, int D_, int NB_>
+__global__ void __launch_bounds__(PASS_THREADS, 2) k_pass(Params P, PassArgs A)
+{
+    using SH = Shape<T, D_, NB_>;
+    constexpr int DM = SH::DM;
+    extern __shared__ __align__(128) unsigned char smem[];
+    SmemHead& H = *reinterpret_cast<SmemHead*>(smem);
+    unsigned char* buf0 = smem + SMEM_HEAD;
+    const SH sh(Prec<T>::lay(P), P.d, P.n);
+    const int S = sh.bytes();
+    const size_t tile_bytes = (size_t)A.tile * S;
+    double* Ds = reinterpret_cast<double*>(buf0 + 2 * tile_bytes);
+    const int d = sh.d(), n = sh.n(), dn = d * n, K = P.K;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    constexpr int B = PASS_THREADS * CPT;
+    const unsigned char* lk = Prec<T>::lk(P);
+
+    // ---- work of this CTA ---------------------------------------------------
+    int64_t r0 = 0, r1 = 0;
+    int64_t nbatch = 0;
+    if (MODE == 0) {
+        const int64_t N = P.sc->n_total;
+        r0 = N * blockIdx.x / gridDim.x;
+        r1 = N * (blockIdx.x + 1) / gridDim.x;
+        int64_t i = r0;
+        while (i < r1) {
+            const int c = find_channel(P.Pc, K, i);
+            const int64_t e = min(r1, P.Pc[c + 1]);
+            nbatch += (e - i + B - 1) / B;
+            i = e;
+        }
+    } else {
+        const int64_t nch = A.nchunks;
+        nbatch = blockIdx.x < nch ? (nch - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    }
+    if (nbatch == 0) return;
+    const int ntiles = A.ntiles;
+    const bool streaming = ntiles > 2;
+    const int64_t total_uses = streaming ? nbatch * ntiles : ntiles;
+
+    auto issue = [&](int64_t u) {
+        const int t = (int)(u % ntiles);
+        const int cnt = min(A.tile, K - t * A.tile);
+        fence_proxy_async_smem();
+        bulk_load(buf0 + (u & 1) * tile_bytes, lk + (size_t)t * tile_bytes, (uint32_t)(cnt * S), &H.bar[u & 1]);
+    };
+    if (tid == 0) {
+        mbar_init(&H.bar[0], 1);
+        mbar_init(&H.bar[1], 1);
+        H.abort = 0;
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (tid == 0) {
+        issue(0);
+        if (total_uses > 1) issue(1);
+    }
+    int64_t u = 0;              // next tile use to consume
+    int64_t issued = total_uses > 1 ? 2 : 1;
+    double wm = 0.0, s1 = 0.0, s2 = 0.0;
+    bool bad = false;
+
+    // integration segment state
+    int64_t i0 = r0;
+    int cseg = -1;
+    int64_t seg_end = 0;
+    double sft = 0.0;
+    // generation chunk state
+    int64_t chunk = blockIdx.x;
+
+    for (int64_t bt = 0; bt < nbatch; ++bt) {
+        int64_t base, end;
+        if (MODE == 0) {
+            if (i0 >= seg_end || cseg < 0) {
+                // new segment of one channel: reset the shared d-values
+                cseg = find_channel(P.Pc, K, i0);
+                seg_end = min(r1, P.Pc[cseg + 1]);
+                sft = P.shift[cseg];
+                for (int q = tid; q < dn; q += PASS_THREADS) Ds[q] = 0.0;
+                s1 = s2 = 0.0;
+                __syncthreads();
+            }
+            base = i0;
+            end = min(seg_end, i0 + B);
+        } else {
+            base = chunk * B;
+            end = min(A.batch, base + B);
+        }
+
+        // ---- phase A: own channel forward map, integrand --------------------
+        T p[CPT][DM], g[CPT], f[CPT], Aexp[CPT];
+        bool skip[CPT], valid[CPT];
+        int cq[CPT];
+        uint32_t jp[CPT][(DM + 3) / 4];
+        uint32_t xacc[CPT];
+#pragma unroll
+        for (int q = 0; q < CPT; ++q) {
+            const int64_t i = base + (int64_t)q * PASS_THREADS + tid;
+            valid[q] = i < end;
+            uint32_t X[DM + 4];
+            call_words<DM + 4>(P, (uint32_t)(valid[q] ? i : base), A.field, MODE == 0 ? d : d + 2, X);
+            int c;
+            if (MODE == 0) {
+                c = cseg;
+                xacc[q] = 0u;
+            } else {
+                uint32_t xc = 0u, xa = 0u;
+#pragma unroll
+                for (int k = 0; k < DM + 4; ++k) {
+                    if (k == d) xc = X[k];
+                    if (k == d + 1) xa = X[k];
+                }
+                c = choose_channel(P, unif64(xc));
+                xacc[q] = xa;
+            }
+            cq[q] = c;
+            T x[DM];
+            int jf[DM];
+            T owngJ, Aq;
+            forward_call<T>(P, sh, c, X, x, p[q], jf, owngJ, Aq);
+            Aexp[q] = Aq;
+#pragma unroll
+            for (int w = 0; w < (DM + 3) / 4; ++w) {
+                uint32_t v = 0;
+#pragma unroll
+                for (int b = 0; b < 4; ++b)
+                    if (4 * w + b < DM) v |= (uint32_t)(jf[4 * w + b] & 0xff) << (8 * b);
+                jp[q][w] = v;
+            }
+            g[q] = Prec<T>::alpha(P, c) * owngJ;
+            f[q] = P.matching ? T(0) : integrand_peaks<T, DM>(P, d, p[q], Aq);
+        }
+
+        // ---- phase B: every channel's term of g(p) (and the matching peaks) --
+        for (int t = 0; t < ntiles; ++t) {
+            // streaming: use u lives in buffer u%2 (phase u/2); otherwise tile t
+            // stays in buffer t after the first batch
+            const int b = streaming ? (int)(u & 1) : t;
+            if (streaming || bt == 0) {
+                if (!mbar_wait_bounded(&H.bar[b], streaming ? (uint32_t)((u >> 1) & 1) : 0u)) {
+                    atomicOr(&P.sc->err, ERR_TIMEOUT);
+                    H.abort = 1;
+                }
+            }
+            if (!H.abort) {
+                const int cnt = min(A.tile, K - t * A.tile);
+                const unsigned char* tb = buf0 + b * tile_bytes;
+                for (int cl = 0; cl < cnt; ++cl) {
+                    const int c2 = t * A.tile + cl;
+                    const T a = Prec<T>::alpha(P, c2);
+                    const bool lookups = (a != T(0)) && !(MODE == 0 && c2 == cseg);
+#pragma unroll
+                    for (int q = 0; q < CPT; ++q) skip[q] = (MODE == 1) && (cq[q] == c2);
+                    channel_body<T, CPT, false>(P, sh, tb + (size_t)cl * S, a, lookups, P.matching != 0, p, Aexp,
+                                                skip, g, f, nullptr);
+                }
+            }
+            __syncthreads();
+            if (H.abort) goto drain;
+            if (streaming && tid == 0 && issued < total_uses) {
+                issue(issued);
+                ++issued;
+            }
+            ++u;
+        }
+
+        // ---- phase C: weights and accumulation ------------------------------
+        if (MODE == 0) {
+#pragma unroll
+            for (int q = 0; q < CPT; ++q) {
+                if (!valid[q]) continue;
+                double w = g[q] > T(0) ? (double)(f[q] / g[q]) : 0.0;
+                if (!isfinite(w)) { bad = true; w = 0.0; }
+                const double dv = w - sft;
+                s1 += dv;
+                s2 += dv * dv;
+                wm = fmax(wm, w);
+                const double w2 = w * w;
+#pragma unroll
+                for (int k = 0; k < DM; ++k)
+                    if (k < d) atomicAdd(&Ds[k * n + ((jp[q][k >> 2] >> (8 * (k & 3))) & 0xff)], w2);
+            }
+            i0 = end;
+            if (i0 >= seg_end) {
+                // end of the segment: flush its sums and d-values
+                s1 = warp_sum(s1);
+                s2 = warp_sum(s2);
+                if (lane == 0) { H.red[0][wid] = s1; H.red[1][wid] = s2; }
+                __syncthreads();
+                if (tid == 0) {
+                    double a = 0.0, bb = 0.0;
+                    for (int q = 0; q < PASS_THREADS / 32; ++q) { a += H.red[0][q]; bb += H.red[1][q]; }
+                    atomicAdd(&P.csum[2 * cseg], a);
+                    atomicAdd(&P.csum[2 * cseg + 1], bb);
+                }
+                double* Dg = P.D + (size_t)cseg * dn;
+                for (int q = tid; q < dn; q += PASS_THREADS) {
+                    const double v = Ds[q];
+                    if (v != 0.0) atomicAdd(&Dg[q], v);
+                }
+                s1 = s2 = 0.0;
+                __syncthreads();
+            }
+        } else {
+            const double wmax = P.sc->wmax_gen;
+            int running = 0;
+            const int64_t cbase = chunk * B;
+#pragma unroll
+            for (int q = 0; q < CPT; ++q) {
+                double w = 0.0;
+                bool acc = false;
+                if (valid[q]) {
+                    w = g[q] > T(0) ? (double)(f[q] / g[q]) : 0.0;
+                    if (!isfinite(w)) { bad = true; w = 0.0; }
+                    wm = fmax(wm, w);
+                    acc = unif64(xacc[q]) * wmax < w;
+                }
+                const unsigned bal = __ballot_sync(0xffffffffu, acc);
+                if (lane == 0) H.wcnt[wid] = __popc(bal);
+                __syncthreads();
+                if (tid == 0) {
+                    int s = 0;
+                    for (int w2 = 0; w2 < PASS_THREADS / 32; ++w2) { H.woff[w2] = s; s += H.wcnt[w2]; }
+                    H.round_total = s;
+                }
+                __syncthreads();
+                if (acc) {
+                    const int pos = running + H.woff[wid] + __popc(bal & ((1u << lane) - 1u));
+                    const int64_t slot = cbase + pos;
+                    unsigned char* rec = A.staging + slot * A.rec_bytes;
+                    float* pf = reinterpret_cast<float*>(rec);
+#pragma unroll
+                    for (int k = 0; k < DM; ++k)
+                        if (k < d) pf[k] = (float)p[q][k];
+                    if (d & 1) pf[d] = 0.0f;
+                    *reinterpret_cast<double*>(rec + A.rec_bytes - 8) = w;
+                    A.callidx[slot] = (uint32_t)(base + (int64_t)q * PASS_THREADS + tid);
+                }
+                running += H.round_total;
+                __syncthreads();
+            }
+            if (tid == 0) A.counts[chunk] = running;
+            chunk += gridDim.x;
+        }
+    }
+
+    // ---- CTA totals --------------------------------------------------------
+    wm = warp_max(wm);
+    if (lane == 0) H.red[2][wid] = wm;
+    if (bad) atomicOr(&P.sc->err, ERR_NONFINITE);
+    __syncthreads();
+    if (tid == 0) {
+        double m = 0.0;
+        for (int q = 0; q < PASS_THREADS / 32; ++q) m = fmax(m, H.red[2][q]);
+        unsigned long long* dst = MODE == 0 ? &P.sc->wmax_bits : &P.sc->gen_bmax_bits;
+        atomicMax(dst, (unsigned long long)__double_as_longlong(m));
+    }
+    return;
+
+drain:
+    // a wait gave up: let this CTA's copies in flight land (bounded), then exit
+    if (tid == 0) {
+        if (streaming) {
+            for (int64_t v = u; v < issued; ++v) mbar_wait_bounded(&H.bar[v & 1], (uint32_t)((v >> 1) & 1));
+        } else {
+            for (int64_t v = u; v < issued; ++v) mbar_wait_bounded(&H.bar[v], 0u);
+        }
+    }
+    __syncthreads();
+}
+
+// Registers the integration and generation kernels of one (T, CPT, D, NB).
+template <typename T, int CPT, int D_, int NB_>
+cudaError_t pass_launch_t(const Params& P, int mode, const PassArgs& A, int grid, size_t smem, cudaStream_t s)
+{
+    if (mode) k_pass<T, 1, CPT, D_, NB_><<<grid, PASS_THREADS, smem, s>>>(P, A);
+    else k_pass<T, 0, CPT, D_, NB_><<<grid, PASS_THREADS, smem, s>>>(P, A);
+    return cudaGetLastError();
+}
+
+template <typename T, int CPT, int D_, int NB_>
+PassVariant make_variant()
+{
+    PassVariant v;
+    v.fp32 = sizeof(T) == 4;
+    v.cpt = CPT;
+    v.D = D_;
+    v.NB = NB_;
+    v.fn[0] = (const void*)k_pass<T, 0, CPT, D_, NB_>;
+    v.fn[1] = (const void*)k_pass<T, 1, CPT, D_, NB_>;
+    v.launch = &pass_launch_t<T, CPT, D_, NB_>;
+    return v;
+}
+
+}  // namespace vamp
