@@ -106,6 +106,29 @@ def _dist():
     return ws, rank, local
 
 
+KERNEL_SOURCES = ["vamp_pass.cuh", "vamp_device.cuh", "vamp_pass_f32_shapes.cu", "vamp_internal.h"]
+
+
+def measured_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or
+    None when the kernel sources changed since the counters were taken."""
+    import hashlib
+    import re
+    h = hashlib.sha256()
+    for s in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1811_09711_gb300", "csrc", s), "rb") as f:
+            h.update(f.read())
+    try:
+        with open(os.path.join(ROOT, "profiles", "k_pass_fp32_collider_d14_k64.md")) as f:
+            txt = f.read()
+    except OSError:
+        return None
+    for m in re.finditer(r"traffic_record: (.+?) (\d+) sha256=([0-9a-f]+)", txt):
+        if m.group(1) == kernel and m.group(3) == h.hexdigest():
+            return int(m.group(2))
+    return None
+
+
 def lookup_ops_per_call(pr) -> float:
     """Algorithmic lane-operations per call charged to the roofline: the K*d
     bin lookups of g(p), 8 lane-ops each (cell index 2, table probe 1, edge
@@ -315,9 +338,10 @@ def run_gpu(args):
     k_ms = ks["sample_ms"] / max(ks["sample_launches"], 1)
     ops = lookup_ops_per_call(pr) * (calls / max(args.steps, 1))
     achieved = ops / (k_ms / 1e3) / 1e12
+    kname = g.kernel_name()
     roof = {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "Tops/s",
-            "frac": achieved / peak_tops, "traffic": None,
-            "kernel": "k_sample<float>", "kernel_ms": k_ms,
+            "frac": achieved / peak_tops, "traffic": measured_traffic(kname),
+            "kernel": kname, "kernel_ms": k_ms,
             "peak_source": f"{n_sm} SMs x 128 lanes x {sm_max:.0f} MHz ({src} max clock)"}
 
     res = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,

@@ -210,6 +210,13 @@ vamp_status vamp_profile(vamp_ctx *ctx, int32_t enable);
 vamp_status vamp_kernel_stats(vamp_ctx *ctx, double *sample_ms, int64_t *sample_launches, double *gen_ms,
                               int64_t *gen_launches);
 
+/* The pass-kernel variant the context uses (chosen at create time by timing
+ * the candidates once per process and shape class): FP32-eval or FP64, calls
+ * per thread, and the (d, n) it is specialised for (0, 0 = any shape).  For
+ * benchmarks and profiles.  Any pointer may be NULL. */
+vamp_status vamp_pass_kernel_info(const vamp_ctx *ctx, int32_t *fp32, int32_t *calls_per_thread,
+                                  int32_t *shape_d, int32_t *shape_n);
+
 /* One sampling pass that allocates nothing, for callers that cannot let a
  * library allocate memory (all device memory owned by the caller's own pool,
  * or a path where an allocation could block or fail unpredictably).  The

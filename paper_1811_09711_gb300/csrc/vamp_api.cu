@@ -555,4 +555,15 @@ vamp_status vamp_kernel_stats(vamp_ctx* c, double* sample_ms, int64_t* sample_la
     return VAMP_OK;
 }
 
+vamp_status vamp_pass_kernel_info(const vamp_ctx* c, int32_t* fp32, int32_t* cpt, int32_t* shape_d,
+                                  int32_t* shape_n)
+{
+    if (!c || !c->var) return VAMP_ERR_INVALID_ARG;
+    if (fp32) *fp32 = c->var->fp32;
+    if (cpt) *cpt = c->var->cpt;
+    if (shape_d) *shape_d = c->var->D;
+    if (shape_n) *shape_n = c->var->NB;
+    return VAMP_OK;
+}
+
 }  // extern "C"

@@ -107,6 +107,9 @@ def load():
         lib.vamp_sample_pass_static.argtypes = [C.POINTER(Config), vp, vp, vp, i64, u32, vp, vp,
                                                 C.POINTER(PassResult), C.c_char_p, i32]
         lib.vamp_sample_pass_static.restype = st
+        lib.vamp_pass_kernel_info.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32),
+                                              C.POINTER(i32)]
+        lib.vamp_pass_kernel_info.restype = st
         lib.vamp_destroy.argtypes = [vp]
         lib.vamp_destroy.restype = None
         lib.vamp_last_error.argtypes = [vp]
@@ -238,6 +241,17 @@ class Vamp:
         self._check(self.lib.vamp_kernel_stats(self.h, C.byref(sm), C.byref(sn), C.byref(gm), C.byref(gn)))
         return {"sample_ms": sm.value, "sample_launches": sn.value, "gen_ms": gm.value,
                 "gen_launches": gn.value}
+
+    def kernel_info(self):
+        f, c, dd, nn = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
+        self._check(self.lib.vamp_pass_kernel_info(self.h, C.byref(f), C.byref(c), C.byref(dd), C.byref(nn)))
+        return {"fp32": f.value, "calls_per_thread": c.value, "shape_d": dd.value, "shape_n": nn.value}
+
+    def kernel_name(self, mode: int = 0) -> str:
+        """Name of the pass kernel as profilers print it."""
+        k = self.kernel_info()
+        t = "float" if k["fp32"] else "double"
+        return f"k_pass<{t}, {mode}, {k['calls_per_thread']}, {k['shape_d']}, {k['shape_n']}>"
 
     # -- state ---------------------------------------------------------------
     def get_state(self):
