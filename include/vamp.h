@@ -217,6 +217,45 @@ vamp_status vamp_kernel_stats(vamp_ctx *ctx, double *sample_ms, int64_t *sample_
 vamp_status vamp_pass_kernel_info(const vamp_ctx *ctx, int32_t *fp32, int32_t *calls_per_thread,
                                   int32_t *shape_d, int32_t *shape_n);
 
+/* ---- many independent integrations in one launch --------------------------
+ * A batch advances n integrations of possibly different d, K, n, calls and
+ * seeds together (all in the same precision): every iteration runs ONE
+ * persistent pass kernel whose CTAs take work items -- up to item_calls
+ * consecutive calls of one channel of one instance -- from an atomic counter,
+ * plus a few multi-instance kernels for allocation, pass results, rebinning
+ * and α.  The paper's analogue is the automatic choice between parallel
+ * modes over channels and over stratification cells (§4.5.2).  Each
+ * iteration is captured once as a CUDA graph and replayed.  Results equal
+ * those of running every instance alone with vamp_create /
+ * vamp_sample_pass / vamp_refine_grids / vamp_update_alpha (same random
+ * streams), up to the order of floating-point sums. */
+typedef struct vamp_batch vamp_batch;
+
+/* Creates the batch on the current device with its own CUDA stream; cfgs[i]
+ * as for vamp_create (all with the same precision).  autotune_tiles = 1: the
+ * first iteration times work-item sizes and shared-memory budgets once and
+ * keeps the fastest; 0: one batch of calls per item, 112 KB per CTA. */
+vamp_status vamp_batch_create(const vamp_config *cfgs, int32_t n, int32_t autotune_tiles, vamp_batch **out);
+
+/* One adaptation iteration of every instance: n_calls[i] calls (host array),
+ * random stream `iteration` (< 2^31), adapt bit 0 = rebin grids, bit 1 =
+ * update α; results[i] (host array of n) receive the pass results.
+ * Synchronises.  NUMERIC / TIMEOUT as for vamp_sample_pass. */
+vamp_status vamp_batch_iterate(vamp_batch *b, const int64_t *n_calls, uint32_t iteration, int32_t adapt,
+                               vamp_pass_result *results);
+
+/* State of one instance into host arrays (any may be NULL), as vamp_get_state. */
+vamp_status vamp_batch_get_state(vamp_batch *b, int32_t instance, double *edges, double *alpha, double *shift,
+                                 double *w_max);
+
+/* The launch shape in use and the autotuner's timings of one pass (tuned and
+ * fixed shape, at an eighth of the first iteration's calls; 0 if untuned). */
+vamp_status vamp_batch_tuning(const vamp_batch *b, int64_t *item_calls, int32_t *budget_kb, double *tuned_ms,
+                              double *fixed_ms);
+
+void vamp_batch_destroy(vamp_batch *b);
+const char *vamp_batch_last_error(const vamp_batch *b);
+
 /* One sampling pass that allocates nothing, for callers that cannot let a
  * library allocate memory (all device memory owned by the caller's own pool,
  * or a path where an allocation could block or fail unpredictably).  The

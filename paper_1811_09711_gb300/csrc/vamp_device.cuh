@@ -236,8 +236,8 @@ template <> struct Prec<float> {
 // Shape policy: D_, NB_ > 0 fix the dimension and the bins at compile time
 // (all block offsets become constants); 0 means "read from the layout".
 // ---------------------------------------------------------------------------
-constexpr int ceil_log2(int v) { return v <= 1 ? 0 : 1 + ceil_log2((v + 1) / 2); }
-constexpr int round_up(int v, int m) { return (v + m - 1) / m * m; }
+__host__ __device__ constexpr int ceil_log2(int v) { return v <= 1 ? 0 : 1 + ceil_log2((v + 1) / 2); }
+__host__ __device__ constexpr int round_up(int v, int m) { return (v + m - 1) / m * m; }
 
 template <typename T>
 __host__ __device__ constexpr BlkLayout make_layout_c(int d, int n)

@@ -91,6 +91,42 @@ std::vector<const PassVariant*> pass_candidates(int fp32, int d, int n);
 // Raises (never lowers) the dynamic shared-memory limit of a kernel.
 cudaError_t ensure_smem(const void* fn, size_t bytes);
 
+// ---- many instances in one launch -------------------------------------------
+// Per-iteration arguments read by the batch kernels (copied from pinned host
+// memory by the first node of the iteration graph).
+struct BatchIter {
+    uint32_t iteration;
+    int32_t adapt;         // bit 0: refine grids, bit 1: update α
+};
+// Work-item bookkeeping of the multi-instance pass kernel.
+struct BatchCtl {
+    long long total;       // work items of this iteration
+    long long next;        // next item to hand out (atomic)
+};
+struct MultiArgs {
+    const Params* inst;          // [n] instance parameters
+    const int* tiles;            // [n] channels per staged tile
+    const int* combine_from;     // [n]
+    const int64_t* ncalls;       // [n] calls requested this iteration
+    const int* pair_off;         // [n+1] first (instance, channel) pair of instance i
+    long long* pair_prefix;      // [npairs+1] items before each pair
+    const int* row_off;          // [n+1] first grid row of instance i (rows = K*d)
+    BatchCtl* ctl;
+    const BatchIter* it;
+    double* results;             // [n][9]: pass result (8) and calls
+    int n_inst;
+    int npairs;
+    int nrows;
+    int max_n;                   // largest bins per axis
+    int64_t item_calls;          // calls per work item (multiple of PASS_THREADS*CPT)
+};
+constexpr int PARAMS_SLOT = 512;  // bytes reserved for an instance's Params in shared memory
+
+cudaError_t launch_batch_begin(const MultiArgs& M, cudaStream_t s);
+cudaError_t launch_batch_after(const MultiArgs& M, cudaStream_t s);  // finish, refine, α, gather
+cudaError_t launch_pass_multi(int fp32, const MultiArgs& M, int grid, size_t smem, cudaStream_t s);
+const void* pass_multi_kernel(int fp32);
+
 cudaError_t launch_begin_pass(const Params& P, int64_t N, cudaStream_t s);
 cudaError_t launch_finish_pass(const Params& P, int combine, cudaStream_t s);
 cudaError_t launch_derive(const Params& P, cudaStream_t s);

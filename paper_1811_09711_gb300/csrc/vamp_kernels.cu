@@ -15,9 +15,9 @@ namespace vamp {
 // ---------------------------------------------------------------------------
 // allocation (R6: N_c = max(N_min, floor(α_c N)) for α_c > 0)
 // ---------------------------------------------------------------------------
-__global__ void k_begin_pass(Params P, int64_t N)
+__device__ void begin_pass_dev(const Params& P, int64_t N)
 {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
+    {
         int64_t acc = 0;
         P.Pc[0] = 0;
         for (int c = 0; c < P.K; ++c) {
@@ -35,12 +35,16 @@ __global__ void k_begin_pass(Params P, int64_t N)
     }
 }
 
+__global__ void k_begin_pass(Params P, int64_t N)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) begin_pass_dev(P, N);
+}
+
 // ---------------------------------------------------------------------------
 // pass result (Eqs. 10, 11 per channel on shifted sums; Eq. 23; R8, R9)
 // ---------------------------------------------------------------------------
-__global__ void k_finish_pass(Params P, int combine)
+__device__ void finish_pass_dev(const Params& P, int combine)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
     Scalars* sc = P.sc;
     double I = 0.0, V = 0.0;
     for (int c = 0; c < P.K; ++c) {
@@ -111,6 +115,11 @@ __global__ void k_finish_pass(Params P, int combine)
     sc->res[7] = chi;
 }
 
+__global__ void k_finish_pass(Params P, int combine)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) finish_pass_dev(P, combine);
+}
+
 // ---------------------------------------------------------------------------
 // lookup blocks of one grid row (Eq. 12 densities, FP32 copies, cell tables)
 // ---------------------------------------------------------------------------
@@ -169,14 +178,11 @@ __global__ void k_derive(Params P)
 // ---------------------------------------------------------------------------
 // rebinning, one warp per (channel, axis) row (Eqs. 14, 15; R2-R4)
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(REFINE_WARPS * 32) k_refine(Params P)
+// One warp rebins grid row `row` of P; ws = 4n+2 doubles of warp scratch.
+__device__ void refine_row_dev(const Params& P, int row, int lane, double* ws)
 {
-    extern __shared__ double rs[];
     const int n = P.n;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int row = blockIdx.x * REFINE_WARPS + wid;
-    if (row >= P.K * P.d) return;
-    double* Dj = rs + (size_t)wid * (4 * n + 2);
+    double* Dj = ws;
     double* m = Dj + n;
     double* C = m + n;          // n+1
     double* eo = C + n + 1;     // n+1
@@ -243,12 +249,20 @@ __global__ void __launch_bounds__(REFINE_WARPS * 32) k_refine(Params P)
     derive_row(P, row, lane);
 }
 
+__global__ void __launch_bounds__(REFINE_WARPS * 32) k_refine(Params P)
+{
+    extern __shared__ double rs[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int row = blockIdx.x * REFINE_WARPS + wid;
+    if (row >= P.K * P.d) return;
+    refine_row_dev(P, row, lane, rs + (size_t)wid * (4 * P.n + 2));
+}
+
 // ---------------------------------------------------------------------------
 // channel weights (Eq. 25 with R5)
 // ---------------------------------------------------------------------------
-__global__ void k_update_alpha(Params P)
+__device__ void update_alpha_dev(const Params& P)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
     const int K = P.K;
     double SU = 0.0, MU = 0.0;
     for (int c = 0; c < K; ++c) {
@@ -273,6 +287,11 @@ __global__ void k_update_alpha(Params P)
     if (tot > 0.0)
         for (int c = 0; c < K; ++c) P.alpha[c] = P.Acum[c] / tot;
     for (int c = 0; c < K; ++c) P.alpha32[c] = (float)P.alpha[c];
+}
+
+__global__ void k_update_alpha(Params P)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) update_alpha_dev(P);
 }
 
 // ---------------------------------------------------------------------------
@@ -405,6 +424,113 @@ __global__ void k_eval(Params P, EvalArgs A)
     A.fgwc[4 * q + 1] = (double)g[0];
     A.fgwc[4 * q + 2] = (double)w;
     A.fgwc[4 * q + 3] = (double)c;
+}
+
+// ---------------------------------------------------------------------------
+// many instances: the small steps of one iteration, one block (or warp) per
+// instance (or grid row)
+// ---------------------------------------------------------------------------
+__global__ void k_batch_begin(MultiArgs M)
+{
+    const int i = blockIdx.x;
+    if (i >= M.n_inst) return;
+    const Params& P = M.inst[i];
+    if (threadIdx.x == 0) begin_pass_dev(P, M.ncalls[i]);
+    const size_t nd = (size_t)P.K * P.d * P.n;
+    for (size_t q = threadIdx.x; q < nd; q += blockDim.x) P.D[q] = 0.0;
+    for (int q = threadIdx.x; q < 2 * P.K; q += blockDim.x) P.csum[q] = 0.0;
+}
+
+// Work items: every (instance, channel) pair with N_c calls gives
+// ceil(N_c / item_calls) items; exclusive prefix over the pairs.
+__global__ void k_batch_items(MultiArgs M)
+{
+    __shared__ long long part[1024];
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int per = (M.npairs + nt - 1) / nt;
+    const int p0 = tid * per, p1 = min(M.npairs, p0 + per);
+    auto items_of = [&](int pr) -> long long {
+        int lo = 0, hi = M.n_inst - 1; // instance with pair_off[i] <= pr
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (M.pair_off[mid] <= pr) lo = mid; else hi = mid - 1;
+        }
+        const long long nc = M.inst[lo].Nc[pr - M.pair_off[lo]];
+        return (nc + M.item_calls - 1) / M.item_calls;
+    };
+    long long s = 0;
+    for (int pr = p0; pr < p1; ++pr) s += items_of(pr);
+    part[tid] = s;
+    __syncthreads();
+    if (tid == 0) {
+        long long a = 0;
+        for (int q = 0; q < nt; ++q) { const long long v = part[q]; part[q] = a; a += v; }
+        M.ctl->total = a;
+        M.ctl->next = 0;
+        M.pair_prefix[M.npairs] = a;
+    }
+    __syncthreads();
+    long long off = part[tid];
+    for (int pr = p0; pr < p1; ++pr) {
+        M.pair_prefix[pr] = off;
+        off += items_of(pr);
+    }
+}
+
+__global__ void k_batch_finish(MultiArgs M)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M.n_inst) return;
+    const Params& P = M.inst[i];
+    finish_pass_dev(P, (int)M.it->iteration >= M.combine_from[i] ? 1 : 0);
+    double* r = M.results + (size_t)i * 9;
+    for (int q = 0; q < 8; ++q) r[q] = P.sc->res[q];
+    r[4] = (double)P.sc->n_total;
+    r[8] = (double)P.sc->err;
+}
+
+__global__ void __launch_bounds__(REFINE_WARPS * 32) k_batch_refine(MultiArgs M)
+{
+    extern __shared__ double rs[];
+    if (!(M.it->adapt & 1)) return;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int row = blockIdx.x * REFINE_WARPS + wid;
+    if (row >= M.nrows) return;
+    int lo = 0, hi = M.n_inst - 1; // instance with row_off[i] <= row
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (M.row_off[mid] <= row) lo = mid; else hi = mid - 1;
+    }
+    refine_row_dev(M.inst[lo], row - M.row_off[lo], lane, rs + (size_t)wid * (4 * M.max_n + 2));
+}
+
+__global__ void k_batch_alpha(MultiArgs M)
+{
+    if (!(M.it->adapt & 2)) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < M.n_inst) update_alpha_dev(M.inst[i]);
+}
+
+cudaError_t launch_batch_begin(const MultiArgs& M, cudaStream_t s)
+{
+    k_batch_begin<<<M.n_inst, 256, 0, s>>>(M);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_batch_items<<<1, 1024, 0, s>>>(M);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_after(const MultiArgs& M, cudaStream_t s)
+{
+    k_batch_finish<<<(M.n_inst + 63) / 64, 64, 0, s>>>(M);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int blocks = (M.nrows + REFINE_WARPS - 1) / REFINE_WARPS;
+    k_batch_refine<<<blocks, REFINE_WARPS * 32, (size_t)REFINE_WARPS * (4 * M.max_n + 2) * sizeof(double), s>>>(M);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_batch_alpha<<<(M.n_inst + 63) / 64, 64, 0, s>>>(M);
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------

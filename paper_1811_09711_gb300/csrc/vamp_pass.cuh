@@ -46,6 +46,145 @@ struct SmemHead {
 };
 static_assert(sizeof(SmemHead) <= SMEM_HEAD, "shared-memory head too large");
 
+// Per-thread state of the CPT calls of one batch.
+template <typename T, int CPT, int DM>
+struct Calls {
+    T p[CPT][DM], g[CPT], f[CPT], Aexp[CPT];
+    bool valid[CPT];
+    int cq[CPT];
+    uint32_t jp[CPT][(DM + 3) / 4];
+    uint32_t xacc[CPT];
+};
+
+// Phase A: Philox words, channel, forward map on the channel's grid, own
+// term of g(p), Gaussian exponent sum; the integrand when peaks are not the
+// channels' maps.  Call q of this thread is base + q*PASS_THREADS + tid.
+template <typename T, int MODE, int CPT, class SH>
+__device__ __forceinline__ void phase_a(const Params& P, const SH& sh, uint32_t field, int64_t base, int64_t end,
+                                        int cseg, Calls<T, CPT, SH::DM>& C)
+{
+    constexpr int DM = SH::DM;
+    const int d = sh.d();
+    const int tid = threadIdx.x;
+#pragma unroll
+    for (int q = 0; q < CPT; ++q) {
+        const int64_t i = base + (int64_t)q * PASS_THREADS + tid;
+        C.valid[q] = i < end;
+        uint32_t X[DM + 4];
+        call_words<DM + 4>(P, (uint32_t)(C.valid[q] ? i : base), field, MODE == 0 ? d : d + 2, X);
+        int c;
+        if (MODE == 0) {
+            c = cseg;
+            C.xacc[q] = 0u;
+        } else {
+            uint32_t xc = 0u, xa = 0u;
+#pragma unroll
+            for (int k = 0; k < DM + 4; ++k) {
+                if (k == d) xc = X[k];
+                if (k == d + 1) xa = X[k];
+            }
+            c = choose_channel(P, unif64(xc));
+            C.xacc[q] = xa;
+        }
+        C.cq[q] = c;
+        T x[DM];
+        int jf[DM];
+        T owngJ, Aq;
+        forward_call<T>(P, sh, c, X, x, C.p[q], jf, owngJ, Aq);
+        C.Aexp[q] = Aq;
+#pragma unroll
+        for (int w = 0; w < (DM + 3) / 4; ++w) {
+            uint32_t v = 0;
+#pragma unroll
+            for (int b = 0; b < 4; ++b)
+                if (4 * w + b < DM) v |= (uint32_t)(jf[4 * w + b] & 0xff) << (8 * b);
+            C.jp[q][w] = v;
+        }
+        C.g[q] = Prec<T>::alpha(P, c) * owngJ;
+        C.f[q] = P.matching ? T(0) : integrand_peaks<T, DM>(P, d, C.p[q], Aq);
+    }
+}
+
+// Phase B for one staged tile: channels t*tile .. of the tile buffer tb.
+template <typename T, int MODE, int CPT, class SH>
+__device__ __forceinline__ void tile_compute(const Params& P, const SH& sh, const unsigned char* tb, int t, int tile,
+                                             int cseg, Calls<T, CPT, SH::DM>& C)
+{
+    const int S = sh.bytes();
+    const int cnt = min(tile, P.K - t * tile);
+    bool skip[CPT];
+    for (int cl = 0; cl < cnt; ++cl) {
+        const int c2 = t * tile + cl;
+        const T a = Prec<T>::alpha(P, c2);
+        const bool lookups = (a != T(0)) && !(MODE == 0 && c2 == cseg);
+#pragma unroll
+        for (int q = 0; q < CPT; ++q) skip[q] = (MODE == 1) && (C.cq[q] == c2);
+        channel_body<T, CPT, false>(P, sh, tb + (size_t)cl * S, a, lookups, P.matching != 0, C.p, C.Aexp, skip,
+                                    C.g, C.f, nullptr);
+    }
+}
+
+// Phase C of an integration batch: shifted sums, max weight and the d-values
+// of the segment's channel in shared memory.
+template <typename T, int CPT, class SH>
+__device__ __forceinline__ void phase_c_int(const SH& sh, const Calls<T, CPT, SH::DM>& C, double sft, double* Ds,
+                                            double& s1, double& s2, double& wm, bool& bad)
+{
+    constexpr int DM = SH::DM;
+    const int d = sh.d(), n = sh.n();
+#pragma unroll
+    for (int q = 0; q < CPT; ++q) {
+        if (!C.valid[q]) continue;
+        double w = C.g[q] > T(0) ? (double)(C.f[q] / C.g[q]) : 0.0;
+        if (!isfinite(w)) { bad = true; w = 0.0; }
+        const double dv = w - sft;
+        s1 += dv;
+        s2 += dv * dv;
+        wm = fmax(wm, w);
+        const double w2 = w * w;
+#pragma unroll
+        for (int k = 0; k < DM; ++k)
+            if (k < d) atomicAdd(&Ds[k * n + ((C.jp[q][k >> 2] >> (8 * (k & 3))) & 0xff)], w2);
+    }
+}
+
+// Flush of a segment: block sums of (s1, s2) and the d-values to global.
+__device__ __forceinline__ void flush_segment(const Params& P, SmemHead& H, int cseg, int dn, double* Ds, double s1,
+                                              double s2)
+{
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    s1 = warp_sum(s1);
+    s2 = warp_sum(s2);
+    if (lane == 0) { H.red[0][wid] = s1; H.red[1][wid] = s2; }
+    __syncthreads();
+    if (tid == 0) {
+        double a = 0.0, bb = 0.0;
+        for (int q = 0; q < PASS_THREADS / 32; ++q) { a += H.red[0][q]; bb += H.red[1][q]; }
+        atomicAdd(&P.csum[2 * cseg], a);
+        atomicAdd(&P.csum[2 * cseg + 1], bb);
+    }
+    double* Dg = P.D + (size_t)cseg * dn;
+    for (int q = tid; q < dn; q += PASS_THREADS) {
+        const double v = Ds[q];
+        if (v != 0.0) atomicAdd(&Dg[q], v);
+    }
+    __syncthreads();
+}
+
+// Block maximum of wm into *dst (non-negative doubles compare as bits).
+__device__ __forceinline__ void block_max_to(SmemHead& H, double wm, unsigned long long* dst)
+{
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    wm = warp_max(wm);
+    if (lane == 0) H.red[2][wid] = wm;
+    __syncthreads();
+    if (tid == 0) {
+        double m = 0.0;
+        for (int q = 0; q < PASS_THREADS / 32; ++q) m = fmax(m, H.red[2][q]);
+        atomicMax(dst, (unsigned long long)__double_as_longlong(m));
+    }
+}
+
 template <typename T, int MODE, int CPT, int D_, int NB_>
 __global__ void __launch_bounds__(PASS_THREADS, 2) k_pass(Params P, PassArgs A)
 {
@@ -136,48 +275,8 @@ __global__ void __launch_bounds__(PASS_THREADS, 2) k_pass(Params P, PassArgs A)
         }
 
         // ---- phase A: own channel forward map, integrand --------------------
-        T p[CPT][DM], g[CPT], f[CPT], Aexp[CPT];
-        bool skip[CPT], valid[CPT];
-        int cq[CPT];
-        uint32_t jp[CPT][(DM + 3) / 4];
-        uint32_t xacc[CPT];
-#pragma unroll
-        for (int q = 0; q < CPT; ++q) {
-            const int64_t i = base + (int64_t)q * PASS_THREADS + tid;
-            valid[q] = i < end;
-            uint32_t X[DM + 4];
-            call_words<DM + 4>(P, (uint32_t)(valid[q] ? i : base), A.field, MODE == 0 ? d : d + 2, X);
-            int c;
-            if (MODE == 0) {
-                c = cseg;
-                xacc[q] = 0u;
-            } else {
-                uint32_t xc = 0u, xa = 0u;
-#pragma unroll
-                for (int k = 0; k < DM + 4; ++k) {
-                    if (k == d) xc = X[k];
-                    if (k == d + 1) xa = X[k];
-                }
-                c = choose_channel(P, unif64(xc));
-                xacc[q] = xa;
-            }
-            cq[q] = c;
-            T x[DM];
-            int jf[DM];
-            T owngJ, Aq;
-            forward_call<T>(P, sh, c, X, x, p[q], jf, owngJ, Aq);
-            Aexp[q] = Aq;
-#pragma unroll
-            for (int w = 0; w < (DM + 3) / 4; ++w) {
-                uint32_t v = 0;
-#pragma unroll
-                for (int b = 0; b < 4; ++b)
-                    if (4 * w + b < DM) v |= (uint32_t)(jf[4 * w + b] & 0xff) << (8 * b);
-                jp[q][w] = v;
-            }
-            g[q] = Prec<T>::alpha(P, c) * owngJ;
-            f[q] = P.matching ? T(0) : integrand_peaks<T, DM>(P, d, p[q], Aq);
-        }
+        Calls<T, CPT, DM> C;
+        phase_a<T, MODE, CPT>(P, sh, A.field, base, end, cseg, C);
 
         // ---- phase B: every channel's term of g(p) (and the matching peaks) --
         for (int t = 0; t < ntiles; ++t) {
@@ -190,19 +289,7 @@ __global__ void __launch_bounds__(PASS_THREADS, 2) k_pass(Params P, PassArgs A)
                     H.abort = 1;
                 }
             }
-            if (!H.abort) {
-                const int cnt = min(A.tile, K - t * A.tile);
-                const unsigned char* tb = buf0 + b * tile_bytes;
-                for (int cl = 0; cl < cnt; ++cl) {
-                    const int c2 = t * A.tile + cl;
-                    const T a = Prec<T>::alpha(P, c2);
-                    const bool lookups = (a != T(0)) && !(MODE == 0 && c2 == cseg);
-#pragma unroll
-                    for (int q = 0; q < CPT; ++q) skip[q] = (MODE == 1) && (cq[q] == c2);
-                    channel_body<T, CPT, false>(P, sh, tb + (size_t)cl * S, a, lookups, P.matching != 0, p, Aexp,
-                                                skip, g, f, nullptr);
-                }
-            }
+            if (!H.abort) tile_compute<T, MODE, CPT>(P, sh, buf0 + b * tile_bytes, t, A.tile, cseg, C);
             __syncthreads();
             if (H.abort) goto drain;
             if (streaming && tid == 0 && issued < total_uses) {
@@ -214,40 +301,12 @@ __global__ void __launch_bounds__(PASS_THREADS, 2) k_pass(Params P, PassArgs A)
 
         // ---- phase C: weights and accumulation ------------------------------
         if (MODE == 0) {
-#pragma unroll
-            for (int q = 0; q < CPT; ++q) {
-                if (!valid[q]) continue;
-                double w = g[q] > T(0) ? (double)(f[q] / g[q]) : 0.0;
-                if (!isfinite(w)) { bad = true; w = 0.0; }
-                const double dv = w - sft;
-                s1 += dv;
-                s2 += dv * dv;
-                wm = fmax(wm, w);
-                const double w2 = w * w;
-#pragma unroll
-                for (int k = 0; k < DM; ++k)
-                    if (k < d) atomicAdd(&Ds[k * n + ((jp[q][k >> 2] >> (8 * (k & 3))) & 0xff)], w2);
-            }
+            phase_c_int<T, CPT>(sh, C, sft, Ds, s1, s2, wm, bad);
             i0 = end;
             if (i0 >= seg_end) {
                 // end of the segment: flush its sums and d-values
-                s1 = warp_sum(s1);
-                s2 = warp_sum(s2);
-                if (lane == 0) { H.red[0][wid] = s1; H.red[1][wid] = s2; }
-                __syncthreads();
-                if (tid == 0) {
-                    double a = 0.0, bb = 0.0;
-                    for (int q = 0; q < PASS_THREADS / 32; ++q) { a += H.red[0][q]; bb += H.red[1][q]; }
-                    atomicAdd(&P.csum[2 * cseg], a);
-                    atomicAdd(&P.csum[2 * cseg + 1], bb);
-                }
-                double* Dg = P.D + (size_t)cseg * dn;
-                for (int q = tid; q < dn; q += PASS_THREADS) {
-                    const double v = Ds[q];
-                    if (v != 0.0) atomicAdd(&Dg[q], v);
-                }
+                flush_segment(P, H, cseg, dn, Ds, s1, s2);
                 s1 = s2 = 0.0;
-                __syncthreads();
             }
         } else {
             const double wmax = P.sc->wmax_gen;
@@ -257,11 +316,11 @@ __global__ void __launch_bounds__(PASS_THREADS, 2) k_pass(Params P, PassArgs A)
             for (int q = 0; q < CPT; ++q) {
                 double w = 0.0;
                 bool acc = false;
-                if (valid[q]) {
-                    w = g[q] > T(0) ? (double)(f[q] / g[q]) : 0.0;
+                if (C.valid[q]) {
+                    w = C.g[q] > T(0) ? (double)(C.f[q] / C.g[q]) : 0.0;
                     if (!isfinite(w)) { bad = true; w = 0.0; }
                     wm = fmax(wm, w);
-                    acc = unif64(xacc[q]) * wmax < w;
+                    acc = unif64(C.xacc[q]) * wmax < w;
                 }
                 const unsigned bal = __ballot_sync(0xffffffffu, acc);
                 if (lane == 0) H.wcnt[wid] = __popc(bal);
@@ -279,7 +338,7 @@ __global__ void __launch_bounds__(PASS_THREADS, 2) k_pass(Params P, PassArgs A)
                     float* pf = reinterpret_cast<float*>(rec);
 #pragma unroll
                     for (int k = 0; k < DM; ++k)
-                        if (k < d) pf[k] = (float)p[q][k];
+                        if (k < d) pf[k] = (float)C.p[q][k];
                     if (d & 1) pf[d] = 0.0f;
                     *reinterpret_cast<double*>(rec + A.rec_bytes - 8) = w;
                     A.callidx[slot] = (uint32_t)(base + (int64_t)q * PASS_THREADS + tid);
@@ -293,16 +352,8 @@ __global__ void __launch_bounds__(PASS_THREADS, 2) k_pass(Params P, PassArgs A)
     }
 
     // ---- CTA totals --------------------------------------------------------
-    wm = warp_max(wm);
-    if (lane == 0) H.red[2][wid] = wm;
     if (bad) atomicOr(&P.sc->err, ERR_NONFINITE);
-    __syncthreads();
-    if (tid == 0) {
-        double m = 0.0;
-        for (int q = 0; q < PASS_THREADS / 32; ++q) m = fmax(m, H.red[2][q]);
-        unsigned long long* dst = MODE == 0 ? &P.sc->wmax_bits : &P.sc->gen_bmax_bits;
-        atomicMax(dst, (unsigned long long)__double_as_longlong(m));
-    }
+    block_max_to(H, wm, MODE == 0 ? &P.sc->wmax_bits : &P.sc->gen_bmax_bits);
     return;
 
 drain:

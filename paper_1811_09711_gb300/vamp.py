@@ -110,6 +110,18 @@ def load():
         lib.vamp_pass_kernel_info.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32),
                                               C.POINTER(i32)]
         lib.vamp_pass_kernel_info.restype = st
+        lib.vamp_batch_create.argtypes = [C.POINTER(Config), i32, i32, C.POINTER(vp)]
+        lib.vamp_batch_create.restype = st
+        lib.vamp_batch_iterate.argtypes = [vp, vp, u32, i32, C.POINTER(PassResult)]
+        lib.vamp_batch_iterate.restype = st
+        lib.vamp_batch_get_state.argtypes = [vp, i32, vp, vp, vp, C.POINTER(dbl)]
+        lib.vamp_batch_get_state.restype = st
+        lib.vamp_batch_tuning.argtypes = [vp, C.POINTER(i64), C.POINTER(i32), C.POINTER(dbl), C.POINTER(dbl)]
+        lib.vamp_batch_tuning.restype = st
+        lib.vamp_batch_destroy.argtypes = [vp]
+        lib.vamp_batch_destroy.restype = None
+        lib.vamp_batch_last_error.argtypes = [vp]
+        lib.vamp_batch_last_error.restype = C.c_char_p
         lib.vamp_destroy.argtypes = [vp]
         lib.vamp_destroy.restype = None
         lib.vamp_last_error.argtypes = [vp]
@@ -292,6 +304,62 @@ class Vamp:
                                              _ptr(x), _ptr(p), _ptr(jf), _ptr(bins), _ptr(fgwc)))
         return {"x": x, "p": p, "jf": jf, "bins": bins, "f": fgwc[:, 0], "g": fgwc[:, 1],
                 "w": fgwc[:, 2], "channel": fgwc[:, 3].astype(np.int64)}
+
+
+class Batch:
+    """Many independent integrations advanced together (vamp_batch_*)."""
+
+    def __init__(self, problems, precision: int = PREC_FP32_EVAL, autotune: bool = True):
+        self.lib = load()
+        self.problems = list(problems)
+        cfgs = (Config * len(self.problems))()
+        self._keep = []
+        for i, pr in enumerate(self.problems):
+            cfg, keep = make_config(pr, precision)
+            cfgs[i] = cfg
+            self._keep.append(keep)
+        self._cfgs = cfgs
+        h = C.c_void_p()
+        rc = self.lib.vamp_batch_create(cfgs, len(self.problems), int(bool(autotune)), C.byref(h))
+        if rc != VAMP_OK:
+            raise VampError(rc, "vamp_batch_create failed")
+        self.h = h
+        self.n = len(self.problems)
+
+    def _check(self, rc):
+        if rc != VAMP_OK:
+            raise VampError(rc, self.lib.vamp_batch_last_error(self.h).decode())
+
+    def iterate(self, n_calls, iteration: int, adapt: int = 3):
+        nc = np.ascontiguousarray(n_calls, np.int64)
+        res = (PassResult * self.n)()
+        self._check(self.lib.vamp_batch_iterate(self.h, _ptr(nc), int(iteration), int(adapt), res))
+        return list(res)
+
+    def get_state(self, i: int):
+        pr = self.problems[i]
+        e = np.zeros((pr.n_channels, pr.d, pr.n_bins + 1), np.float64)
+        a = np.zeros(pr.n_channels, np.float64)
+        s = np.zeros(pr.n_channels, np.float64)
+        wm = C.c_double()
+        self._check(self.lib.vamp_batch_get_state(self.h, int(i), _ptr(e), _ptr(a), _ptr(s), C.byref(wm)))
+        return {"edges": e, "alpha": a, "shift": s, "w_max": wm.value}
+
+    def tuning(self):
+        ic, bk, tm, fm = C.c_int64(), C.c_int32(), C.c_double(), C.c_double()
+        self._check(self.lib.vamp_batch_tuning(self.h, C.byref(ic), C.byref(bk), C.byref(tm), C.byref(fm)))
+        return {"item_calls": ic.value, "budget_kb": bk.value, "tuned_ms": tm.value, "fixed_ms": fm.value}
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.vamp_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def sample_pass_static(problem, precision: int, edges_ptr: int, alpha_ptr: int, shift_ptr: int,
