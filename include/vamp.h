@@ -48,7 +48,8 @@ typedef enum {
     VAMP_ERR_CUDA = 3,        /* a CUDA runtime call failed (message has the name) */
     VAMP_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up */
     VAMP_ERR_NUMERIC = 5,     /* a non-finite weight was seen (the call still completed) */
-    VAMP_ERR_STATE = 6        /* call out of order, e.g. refine before any pass */
+    VAMP_ERR_STATE = 6,       /* call out of order, e.g. refine before any pass */
+    VAMP_ERR_LIMIT = 7        /* a served request reached its generation call limit (events are partial) */
 } vamp_status;
 
 typedef enum {
@@ -255,6 +256,73 @@ vamp_status vamp_batch_tuning(const vamp_batch *b, int64_t *item_calls, int32_t 
 
 void vamp_batch_destroy(vamp_batch *b);
 const char *vamp_batch_last_error(const vamp_batch *b);
+
+/* ---- request serving with continuous batching -----------------------------
+ * A request is one whole use of the method (§3, §3.5): `iterations`
+ * adaptation iterations of `calls` calls each (rebinning, Eq. 14, and α
+ * update, Eq. 25, after every pass; passes from combine_from on are
+ * combined), then n_events unweighted events (§3.5) from the adapted grids,
+ * generation stream gen_id = 0.  A scheduler thread admits queued requests
+ * while fewer than max_slots are active and their device memory stays within
+ * mem_budget_bytes (a request that alone exceeds the budget runs when nothing
+ * else does); every scheduler tick advances all integrating requests by one
+ * iteration in one multi-instance launch (a request that arrives meanwhile
+ * joins the next tick) and keeps one generation batch of every generating
+ * request in flight on the request's own stream.  Each request's results and
+ * events equal those of the same request run alone through vamp_create /
+ * vamp_sample_pass (iteration i) / vamp_refine_grids / vamp_update_alpha /
+ * vamp_generate(gen_id 0), up to the order of floating-point sums. */
+typedef struct vamp_server vamp_server;
+
+typedef struct vamp_request_result {
+    uint64_t id;
+    int32_t status;             /* vamp_status of the request */
+    int32_t iterations;         /* iterations completed */
+    vamp_pass_result result;    /* the last pass, with the running combination */
+    int64_t calls_total;        /* Σ N' over the iterations */
+    int64_t events_written;
+    int64_t events_calls_used;
+    int64_t events_overweight;
+    double queue_s;             /* submit -> admission (seconds) */
+    double latency_s;           /* submit -> completion (seconds) */
+} vamp_request_result;
+
+/* Starts the scheduler thread on the current device.  precision: every
+ * request is run in this precision (its cfg->precision is ignored). */
+vamp_status vamp_server_create(int32_t max_slots, int64_t mem_budget_bytes, int32_t precision, vamp_server **out);
+
+/* Queues a request (cfg copied during the call).  iterations >= 1;
+ * calls >= 1; max_gen_calls: generation stops after the first batch that
+ * brings the calls spent on events to at least this many (0 = at most 2^16
+ * batches) and the request ends with VAMP_ERR_LIMIT and the events so far --
+ * a poorly adapted request can have a tiny unweighting efficiency; dev_records: device buffer of n_events *
+ * vamp_record_bytes(cfg->d) bytes, 8-byte aligned, owned by the caller and
+ * left untouched by anything but this request until its result is polled
+ * (may be NULL when n_events = 0).  *id_out receives the request id.
+ * INVALID_ARG for a bad cfg or arguments; nothing is queued then. */
+vamp_status vamp_server_submit(vamp_server *s, const vamp_config *cfg, int32_t iterations, int64_t calls,
+                               int64_t n_events, int64_t max_gen_calls, void *dev_records, uint64_t *id_out);
+
+/* Moves up to max_results completed requests (completion order) into out
+ * (host); returns how many. */
+int32_t vamp_server_poll(vamp_server *s, vamp_request_result *out, int32_t max_results);
+
+/* Waits until no request is queued or active (TIMEOUT after timeout_s). */
+vamp_status vamp_server_wait_idle(vamp_server *s, double timeout_s);
+
+/* Counters since creation: scheduler ticks that ran an integration launch,
+ * integration calls, events written; device bytes held by active requests. */
+vamp_status vamp_server_stats(const vamp_server *s, int64_t *ticks, int64_t *calls, int64_t *events,
+                              int64_t *mem_in_use);
+
+/* Scheduler load as of its last tick: requests queued, integrating and
+ * generating; generation batches launched since creation. */
+vamp_status vamp_server_load(const vamp_server *s, int32_t *queued, int32_t *integrating, int32_t *generating,
+                             int64_t *gen_batches);
+
+/* Stops the scheduler (queued requests are dropped; active ones are left
+ * unfinished) and frees everything. */
+void vamp_server_destroy(vamp_server *s);
 
 /* One sampling pass that allocates nothing, for callers that cannot let a
  * library allocate memory (all device memory owned by the caller's own pool,

@@ -201,6 +201,7 @@ const char* vamp_status_string(vamp_status s)
     case VAMP_ERR_TIMEOUT: return "VAMP_ERR_TIMEOUT";
     case VAMP_ERR_NUMERIC: return "VAMP_ERR_NUMERIC";
     case VAMP_ERR_STATE: return "VAMP_ERR_STATE";
+    case VAMP_ERR_LIMIT: return "VAMP_ERR_LIMIT";
     }
     return "VAMP_ERR_UNKNOWN";
 }

@@ -32,6 +32,7 @@ struct vamp_batch {
     int* d_tiles = nullptr;
     int* d_comb = nullptr;
     int64_t* d_ncalls = nullptr;
+    uint32_t* d_iter = nullptr;
     int* d_pair_off = nullptr;
     long long* d_pair_prefix = nullptr;
     int* d_row_off = nullptr;
@@ -41,6 +42,7 @@ struct vamp_batch {
     // pinned host mirrors
     vamp::BatchIter* h_it = nullptr;
     int64_t* h_ncalls = nullptr;
+    uint32_t* h_iter = nullptr;
     double* h_results = nullptr;
     // launch shape
     int64_t item_calls = 0;
@@ -80,6 +82,7 @@ vamp::MultiArgs margs(const vamp_batch* b)
     M.tiles = b->d_tiles;
     M.combine_from = b->d_comb;
     M.ncalls = b->d_ncalls;
+    M.iter = b->d_iter;
     M.pair_off = b->d_pair_off;
     M.pair_prefix = b->d_pair_prefix;
     M.row_off = b->d_row_off;
@@ -136,6 +139,7 @@ vamp_status enqueue_iteration(vamp_batch* b, bool pass_only)
 {
     BCK(b, cudaMemcpyAsync(b->d_it, b->h_it, sizeof(vamp::BatchIter), cudaMemcpyHostToDevice, b->stream));
     BCK(b, cudaMemcpyAsync(b->d_ncalls, b->h_ncalls, b->n * sizeof(int64_t), cudaMemcpyHostToDevice, b->stream));
+    BCK(b, cudaMemcpyAsync(b->d_iter, b->h_iter, b->n * sizeof(uint32_t), cudaMemcpyHostToDevice, b->stream));
     const vamp::MultiArgs M = margs(b);
     BCK(b, vamp::launch_batch_begin(M, b->stream));
     BCK(b, vamp::launch_pass_multi(b->fp32, M, b->grid, b->smem, b->stream));
@@ -155,6 +159,7 @@ vamp_status autotune(vamp_batch* b, const int64_t* n_calls)
     for (int i = 0; i < b->n; ++i) b->h_ncalls[i] = std::max<int64_t>(1, n_calls[i] / 8);
     b->h_it->iteration = 0x7fffffffu;
     b->h_it->adapt = 0;
+    for (int i = 0; i < b->n; ++i) b->h_iter[i] = 0x7fffffffu;
     cudaEvent_t e0, e1;
     BCK(b, cudaEventCreate(&e0));
     BCK(b, cudaEventCreate(&e1));
@@ -209,6 +214,7 @@ void vamp_batch_destroy(vamp_batch* b)
     cudaFree(b->arena);
     cudaFreeHost(b->h_it);
     cudaFreeHost(b->h_ncalls);
+    cudaFreeHost(b->h_iter);
     cudaFreeHost(b->h_results);
     if (b->stream) cudaStreamDestroy(b->stream);
     if (prev >= 0 && prev != b->dev) cudaSetDevice(prev);
@@ -270,6 +276,8 @@ vamp_status vamp_batch_create(const vamp_config* cfgs, int32_t n, int32_t autotu
     total += a256((size_t)n * 4);
     const size_t o_nc = total;
     total += a256((size_t)n * 8);
+    const size_t o_itr = total;
+    total += a256((size_t)n * 4);
     const size_t o_po = total;
     total += a256((size_t)(n + 1) * 4);
     const size_t o_pp = total;
@@ -289,6 +297,7 @@ vamp_status vamp_batch_create(const vamp_config* cfgs, int32_t n, int32_t autotu
     if (e == cudaSuccess) e = cudaMalloc(&b->arena, total);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_it, sizeof(vamp::BatchIter));
     if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_ncalls, (size_t)n * 8);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_iter, (size_t)n * 4);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_results, (size_t)n * 9 * 8);
     if (e != cudaSuccess) {
         vamp_batch_destroy(b);
@@ -299,6 +308,7 @@ vamp_status vamp_batch_create(const vamp_config* cfgs, int32_t n, int32_t autotu
     b->d_tiles = (int*)(base + o_tiles);
     b->d_comb = (int*)(base + o_comb);
     b->d_ncalls = (int64_t*)(base + o_nc);
+    b->d_iter = (uint32_t*)(base + o_itr);
     b->d_pair_off = (int*)(base + o_po);
     b->d_pair_prefix = (long long*)(base + o_pp);
     b->d_row_off = (int*)(base + o_ro);
@@ -360,7 +370,10 @@ vamp_status vamp_batch_iterate(vamp_batch* b, const int64_t* n_calls, uint32_t i
         drop_graph(b);
     }
     if (st == VAMP_OK) {
-        for (int i = 0; i < b->n; ++i) b->h_ncalls[i] = n_calls[i];
+        for (int i = 0; i < b->n; ++i) {
+            b->h_ncalls[i] = n_calls[i];
+            b->h_iter[i] = iteration;
+        }
         b->h_it->iteration = iteration;
         b->h_it->adapt = adapt;
         if (!b->exec) {

@@ -25,7 +25,6 @@ __global__ void __launch_bounds__(PASS_THREADS, 2) k_pass_multi(MultiArgs M)
     __shared__ long long s_item;
     constexpr int B = PASS_THREADS * CPT;
     const int tid = threadIdx.x;
-    const uint32_t field = M.it->iteration;
     if (tid == 0) {
         mbar_init(&H.bar[0], 1);
         mbar_init(&H.bar[1], 1);
@@ -98,7 +97,7 @@ __global__ void __launch_bounds__(PASS_THREADS, 2) k_pass_multi(MultiArgs M)
         for (int64_t bt = 0; bt < nb; ++bt) {
             const int64_t base = a + bt * B, end = min(b, base + B);
             Calls<T, CPT, SH::DM> C;
-            phase_a<T, 0, CPT>(P, sh, field, base, end, c, C);
+            phase_a<T, 0, CPT>(P, sh, M.iter[inst], base, end, c, C);
             for (int t = 0; t < ntiles; ++t) {
                 const int bb = streaming ? (int)(u & 1) : t;
                 if (streaming || bt == 0) {

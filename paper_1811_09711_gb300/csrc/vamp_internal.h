@@ -108,6 +108,7 @@ struct MultiArgs {
     const int* tiles;            // [n] channels per staged tile
     const int* combine_from;     // [n]
     const int64_t* ncalls;       // [n] calls requested this iteration
+    const uint32_t* iter;        // [n] iteration index (random stream) of each instance
     const int* pair_off;         // [n+1] first (instance, channel) pair of instance i
     long long* pair_prefix;      // [npairs+1] items before each pair
     const int* row_off;          // [n+1] first grid row of instance i (rows = K*d)

@@ -482,7 +482,7 @@ __global__ void k_batch_finish(MultiArgs M)
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= M.n_inst) return;
     const Params& P = M.inst[i];
-    finish_pass_dev(P, (int)M.it->iteration >= M.combine_from[i] ? 1 : 0);
+    finish_pass_dev(P, (int)M.iter[i] >= M.combine_from[i] ? 1 : 0);
     double* r = M.results + (size_t)i * 9;
     for (int q = 0; q < 8; ++q) r[q] = P.sc->res[q];
     r[4] = (double)P.sc->n_total;

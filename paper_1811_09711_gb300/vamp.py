@@ -17,7 +17,7 @@ import numpy as np
 from . import build as _build
 
 VAMP_OK, VAMP_ERR_INVALID_ARG, VAMP_ERR_OOM, VAMP_ERR_CUDA, VAMP_ERR_TIMEOUT, \
-    VAMP_ERR_NUMERIC, VAMP_ERR_STATE = range(7)
+    VAMP_ERR_NUMERIC, VAMP_ERR_STATE, VAMP_ERR_LIMIT = range(8)
 PREC_FP64, PREC_FP32_EVAL = 0, 1
 
 _lock = threading.Lock()
@@ -31,7 +31,8 @@ class VampError(RuntimeError):
 
 
 _STATUS = {0: "VAMP_OK", 1: "VAMP_ERR_INVALID_ARG", 2: "VAMP_ERR_OOM", 3: "VAMP_ERR_CUDA",
-           4: "VAMP_ERR_TIMEOUT", 5: "VAMP_ERR_NUMERIC", 6: "VAMP_ERR_STATE"}
+           4: "VAMP_ERR_TIMEOUT", 5: "VAMP_ERR_NUMERIC", 6: "VAMP_ERR_STATE",
+           7: "VAMP_ERR_LIMIT"}
 
 
 class MapDesc(C.Structure):
@@ -64,6 +65,13 @@ class PassResult(C.Structure):
 
     def __repr__(self):
         return f"PassResult({self.as_dict()})"
+
+
+class RequestResult(C.Structure):
+    _fields_ = [("id", C.c_uint64), ("status", C.c_int32), ("iterations", C.c_int32),
+                ("result", PassResult), ("calls_total", C.c_int64), ("events_written", C.c_int64),
+                ("events_calls_used", C.c_int64), ("events_overweight", C.c_int64),
+                ("queue_s", C.c_double), ("latency_s", C.c_double)]
 
 
 def load():
@@ -122,6 +130,20 @@ def load():
         lib.vamp_batch_destroy.restype = None
         lib.vamp_batch_last_error.argtypes = [vp]
         lib.vamp_batch_last_error.restype = C.c_char_p
+        lib.vamp_server_create.argtypes = [i32, i64, i32, C.POINTER(vp)]
+        lib.vamp_server_create.restype = st
+        lib.vamp_server_submit.argtypes = [vp, C.POINTER(Config), i32, i64, i64, i64, vp, C.POINTER(C.c_uint64)]
+        lib.vamp_server_submit.restype = st
+        lib.vamp_server_poll.argtypes = [vp, C.POINTER(RequestResult), i32]
+        lib.vamp_server_poll.restype = i32
+        lib.vamp_server_wait_idle.argtypes = [vp, dbl]
+        lib.vamp_server_wait_idle.restype = st
+        lib.vamp_server_stats.argtypes = [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)]
+        lib.vamp_server_stats.restype = st
+        lib.vamp_server_load.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32), C.POINTER(i64)]
+        lib.vamp_server_load.restype = st
+        lib.vamp_server_destroy.argtypes = [vp]
+        lib.vamp_server_destroy.restype = None
         lib.vamp_destroy.argtypes = [vp]
         lib.vamp_destroy.restype = None
         lib.vamp_last_error.argtypes = [vp]
@@ -353,6 +375,62 @@ class Batch:
     def close(self):
         if getattr(self, "h", None):
             self.lib.vamp_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching request loop (vamp_server_*): submit whole
+    integrate-then-generate requests, poll completed ones."""
+
+    def __init__(self, max_slots: int = 64, mem_budget_bytes: int = 8 << 30, precision: int = PREC_FP32_EVAL):
+        self.lib = load()
+        self.precision = precision
+        h = C.c_void_p()
+        rc = self.lib.vamp_server_create(int(max_slots), int(mem_budget_bytes), int(precision), C.byref(h))
+        if rc != VAMP_OK:
+            raise VampError(rc, "vamp_server_create failed")
+        self.h = h
+
+    def submit(self, problem, iterations: int, calls: int, n_events: int = 0, records_ptr: int = 0,
+               max_gen_calls: int = 0) -> int:
+        cfg, keep = make_config(problem, self.precision)
+        rid = C.c_uint64()
+        rc = self.lib.vamp_server_submit(self.h, C.byref(cfg), int(iterations), int(calls), int(n_events),
+                                         int(max_gen_calls), C.c_void_p(records_ptr or None), C.byref(rid))
+        del keep  # the server copied the description
+        if rc != VAMP_OK:
+            raise VampError(rc, "vamp_server_submit rejected the request")
+        return rid.value
+
+    def poll(self, max_results: int = 256):
+        buf = (RequestResult * max_results)()
+        k = self.lib.vamp_server_poll(self.h, buf, int(max_results))
+        return [buf[i] for i in range(k)]
+
+    def wait_idle(self, timeout_s: float = 600.0):
+        rc = self.lib.vamp_server_wait_idle(self.h, float(timeout_s))
+        if rc != VAMP_OK:
+            raise VampError(rc, "requests still pending")
+
+    def stats(self):
+        t, c, e, m = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64()
+        self.lib.vamp_server_stats(self.h, C.byref(t), C.byref(c), C.byref(e), C.byref(m))
+        return {"ticks": t.value, "calls": c.value, "events": e.value, "mem_in_use": m.value}
+
+    def load(self):
+        q, i, g, b = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int64()
+        self.lib.vamp_server_load(self.h, C.byref(q), C.byref(i), C.byref(g), C.byref(b))
+        return {"queued": q.value, "integrating": i.value, "generating": g.value, "gen_batches": b.value}
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.vamp_server_destroy(self.h)
             self.h = None
 
     def __del__(self):

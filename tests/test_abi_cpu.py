@@ -41,6 +41,7 @@ def test_library_exports_every_declared_symbol(lib):
 def test_status_strings_and_record_bytes(lib):
     assert lib.vamp_status_string(0) == b"VAMP_OK"
     assert lib.vamp_status_string(6) == b"VAMP_ERR_STATE"
+    assert lib.vamp_status_string(7) == b"VAMP_ERR_LIMIT"
     assert lib.vamp_last_error(None) == b""
     assert [lib.vamp_record_bytes(d) for d in (1, 2, 3, 14, 16)] == [16, 16, 24, 64, 72]
 
@@ -106,3 +107,42 @@ def test_decode_records_layout():
     raw[16:24] = np.frombuffer(np.array([7.25]).tobytes(), np.uint8)
     p, w = V.decode_records(raw, d)
     assert p.shape == (2, 3) and list(p[0]) == [1.5, 2.5, 3.5] and w[0] == 7.25
+
+
+def test_server_null_arguments(lib):
+    h = C.c_void_p()
+    assert lib.vamp_server_create(0, 1 << 30, 1, C.byref(h)) == V.VAMP_ERR_INVALID_ARG and not h.value
+    assert lib.vamp_server_create(4, 0, 1, C.byref(h)) == V.VAMP_ERR_INVALID_ARG
+    assert lib.vamp_server_create(4, 1 << 30, 2, C.byref(h)) == V.VAMP_ERR_INVALID_ARG
+    cfg, keep = V.make_config(P.bw_gauss())
+    rid = C.c_uint64()
+    assert lib.vamp_server_submit(None, C.byref(cfg), 1, 100, 0, 0, None, C.byref(rid)) == V.VAMP_ERR_INVALID_ARG
+    assert lib.vamp_server_poll(None, None, 4) == 0
+    assert lib.vamp_server_wait_idle(None, 1.0) == V.VAMP_ERR_INVALID_ARG
+    lib.vamp_server_destroy(None)
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The binding's ctypes structures have the C header's sizes and offsets
+    (compiled with the host C compiler)."""
+    structs = {
+        "vamp_map_desc": V.MapDesc, "vamp_config": V.Config, "vamp_pass_result": V.PassResult,
+        "vamp_request_result": V.RequestResult,
+    }
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "vamp.h"', "int main(void) {"]
+    for cname, cls in structs.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in cls._fields_:
+            lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    import subprocess
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, cls in structs.items():
+        assert got[(cname, "size")] == C.sizeof(cls), cname
+        for f, _ in cls._fields_:
+            assert got[(cname, f)] == getattr(cls, f).offset, (cname, f)
