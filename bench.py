@@ -16,6 +16,14 @@ through pinned host buffers every step (host->device set_state, pass,
 refine, α, device->host get_state).  The FP64 path and unweighted-event
 generation (1e6 events) are measured in the same run and reported beside it.
 
+`batch`: 256 uneven integrations (d in 2..16, K log-uniform in 1..64, calls
+log-uniform in 1e4..1e7, bins in {20, 50, 100}) advanced together, calls/s
+with autotuned and with fixed work items.  `serving`: a Poisson stream of
+integrate-then-generate requests (200 req/s over a 60 s arrival window,
+10 iterations each, 1e3..1e5 events each, 120 GB device budget) through the
+continuous-batching server, wall-clock throughput and p50/p99 latency, for
+the FP32-eval form and (over a shorter window) the FP64 form.
+
 --impl reference times the FP64 CPU oracle (the only reference this method
 has) on bounded samples of the same workload on the host cores.
 """
@@ -151,6 +159,77 @@ def cpu_oracle_rate(pr, seconds: float, threads: int):
     r = o.sample_pass(n2, 1, n_threads=threads)
     dt2 = time.perf_counter() - t
     return r.n_calls / dt2, r.n_calls, dt2
+
+
+def run_batch(V, P, n_inst: int, iters: int):
+    """256 uneven integrations advanced together (one persistent launch per
+    pass, iterations replayed as a CUDA graph): calls/s with the autotuned
+    work-item shape and with the fixed one."""
+    probs = P.batch(n_inst)
+    out = {"instances": n_inst, "iterations": iters,
+           "calls_per_iteration": int(sum(p.calls for p in probs))}
+    for tag, tune in (("tuned", True), ("fixed", False)):
+        b = V.Batch(probs, precision=V.PREC_FP32_EVAL, autotune=tune)
+        nc = [p.calls for p in probs]
+        b.iterate(nc, 0)  # tuning (if any) and graph capture
+        t = time.perf_counter()
+        calls = 0
+        for it in range(1, iters + 1):
+            calls += sum(r.n_calls for r in b.iterate(nc, it))
+        dt = time.perf_counter() - t
+        out[tag] = {"calls_per_s": calls / dt, "ms_per_iteration": 1e3 * dt / iters}
+        if tune:
+            out["tuning"] = b.tuning()
+        b.close()
+    out["speedup_tuned"] = out["tuned"]["calls_per_s"] / out["fixed"]["calls_per_s"]
+    return out
+
+
+def run_serving(V, P, torch, dev, precision: int, rate: float, seconds: float, budget: int, slots: int,
+                iterations: int, gen_cap: int):
+    """Poisson stream of integrate-then-generate requests through the
+    continuous-batching server: wall-clock throughput and per-request
+    latency (submit to completion)."""
+    import numpy as np
+    reqs = P.serving_stream(rate_per_s=rate, duration_s=seconds, seed=5)
+    rbs = [V.record_bytes(r.problem.d) for r in reqs]
+    offs, tot = [], 0
+    for r, rb in zip(reqs, rbs):
+        offs.append(tot)
+        tot += (r.problem.n_events * rb + 255) // 256 * 256
+    buf = torch.empty(max(tot, 256), dtype=torch.uint8, device=dev)
+    base = buf.data_ptr()
+    srv = V.Server(max_slots=slots, mem_budget_bytes=budget, precision=precision)
+    w = P.serving_stream(rate_per_s=rate, duration_s=1.0, seed=6, max_requests=4)
+    for r in w:  # warm-up: kernels loaded, shared-memory limits raised
+        srv.submit(r.problem, 2, 10_000, 100, base, max_gen_calls=gen_cap)
+    srv.wait_idle(600.0)
+    srv.poll(64)
+    s0 = srv.stats()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for r, off in zip(reqs, offs):
+        now = time.perf_counter() - t0
+        if r.arrival_s > now:
+            time.sleep(r.arrival_s - now)
+        srv.submit(r.problem, iterations, r.problem.calls, r.problem.n_events, base + off, max_gen_calls=gen_cap)
+    srv.wait_idle(3600.0)
+    wall = time.perf_counter() - t0
+    res = srv.poll(len(reqs) + 16)
+    s1 = srv.stats()
+    srv.close()
+    lat = np.array([r.latency_s for r in res]) * 1e3
+    que = np.array([r.queue_s for r in res]) * 1e3
+    calls = s1["calls"] - s0["calls"]
+    events = s1["events"] - s0["events"]
+    return {"requests": len(res), "offered_req_per_s": rate, "arrival_window_s": seconds,
+            "iterations_per_request": iterations, "wall_s": wall, "req_per_s": len(res) / wall,
+            "calls_per_s": calls / wall, "events_per_s": events / wall,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "queue_p50_ms": float(np.percentile(que, 50)), "queue_p99_ms": float(np.percentile(que, 99)),
+            "ticks": s1["ticks"] - s0["ticks"], "limit_hit": int(sum(r.status == V.VAMP_ERR_LIMIT for r in res)),
+            "failed": int(sum(r.status not in (V.VAMP_OK, V.VAMP_ERR_LIMIT) for r in res)),
+            "slots": slots, "budget_gb": budget / 1e9}
 
 
 def run_reference(args):
@@ -330,6 +409,18 @@ def run_gpu(args):
     ms64, calls64, _ = timed_steps(g64, f64_steps, it + 1, 0)
     fp64_rate = calls64 / (sum(ms64) / 1e3)
 
+    # ---- many uneven integrations in one launch; the request stream ----------
+    batch = run_batch(V, P, 256, args.batch_iters) if args.batch_iters > 0 else None
+    serving = None
+    if args.serve_seconds > 0 and rank == 0:
+        cap = 64 << 20
+        serving = {"fp32_eval": run_serving(V, P, torch, dev, V.PREC_FP32_EVAL, args.serve_rate, args.serve_seconds,
+                                            120 * 10**9, args.serve_slots, 10, cap)}
+        if args.serve_seconds_fp64 > 0:
+            serving["fp64"] = run_serving(V, P, torch, dev, V.PREC_FP64, args.serve_rate, args.serve_seconds_fp64,
+                                          120 * 10**9, args.serve_slots, 10, cap)
+        serving["generation_call_limit"] = cap
+
     # ---- roofline of the dominant kernel (FP32-eval sampling kernel) ----------
     peaks, src = _peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
@@ -358,6 +449,10 @@ def run_gpu(args):
                          "efficiency": last.efficiency, "combined": last.combined,
                          "combined_sigma": last.combined_sigma, "chi2_dof": last.chi2_dof},
            "e2e": e2e, "gpu_launches": 5 * args.steps, "roofline": roof, "clocks": clk}
+    if batch is not None:
+        res["batch"] = batch
+    if serving is not None:
+        res["serving"] = serving
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
         thr = os.cpu_count() or 1
         v, ncall, dt = cpu_oracle_rate(base, args.cpu_seconds, thr)
@@ -378,6 +473,11 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--batch-iters", type=int, default=3, help="timed iterations of the 256-instance batch (0: skip)")
+    ap.add_argument("--serve-seconds", type=float, default=60.0, help="arrival window of the request stream (0: skip)")
+    ap.add_argument("--serve-seconds-fp64", type=float, default=2.0, help="arrival window for the FP64 form")
+    ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--serve-slots", type=int, default=256)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

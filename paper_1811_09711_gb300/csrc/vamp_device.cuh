@@ -14,6 +14,9 @@
 // The cell table of a row splits [0,1) into L = 2^lshift equal cells and
 // stores for cell q the bin containing q/L (byte L+1 holds the row's span:
 // the most bins any cell overlaps), so a lookup starts next to its answer.
+// Density entry n repeats entry n-1, so that a probe of edge ξ_n = 1 by a
+// point at (or rounded past) 1 needs no bounds check: it lands on entry n
+// with the last bin's density.
 #pragma once
 
 #include <cstdint>
@@ -66,7 +69,7 @@ struct ChanHdr {
 struct BlkLayout {
     int H;         // header bytes
     int Es;        // edges per row (>= n+1, padded)
-    int Dn;        // densities per row (>= n, padded)
+    int Dn;        // densities per row (>= n+1, padded; entry n repeats entry n-1)
     int Ts;        // table bytes per row (>= L+2, padded)
     int R;         // row stride in bytes
     int lshift;    // L = 2^lshift cells per row
@@ -192,6 +195,7 @@ template <> struct Prec<double> {
     static __device__ __forceinline__ double pow02(double v) { return pow(v, 0.2); }
     static __device__ __forceinline__ double powm08(double v) { return pow(v, -0.8); }
     static __device__ __forceinline__ double exp2_(double v) { return exp2(v); }
+    static __device__ __forceinline__ double div(double a, double b) { return a / b; }
     static __device__ __forceinline__ double tiny() { return 2.2250738585072014e-308; }
     // e <= x for the non-negative edges: compare bit patterns (integer pipe)
     static __device__ __forceinline__ bool le(double e, double x)
@@ -222,13 +226,17 @@ template <> struct Prec<float> {
     static __device__ __forceinline__ float pow02(float v) { return exp2f(0.2f * __log2f(v)); }
     static __device__ __forceinline__ float powm08(float v) { return exp2f(-0.8f * __log2f(v)); }
     static __device__ __forceinline__ float exp2_(float v) { return exp2f(v); }
+    // Jacobian factors of the FP32-eval form: reciprocal-based quotient
+    // (within 2 ulp for the normal denominators that occur here)
+    static __device__ __forceinline__ float div(float a, float b) { return __fdividef(a, b); }
     static __device__ __forceinline__ float tiny() { return 1.17549435e-38f; }
     static __device__ __forceinline__ bool le(float e, float x) { return e <= x; }
+    // floor(x L) of x clamped to [0, 1], in [0, L]: x L + 2^23 rounded toward
+    // zero is exact and its low mantissa bits are the integer part
     static __device__ __forceinline__ int cell(float x, int lshift)
     {
-        const float xc = fminf(fmaxf(x, 0.0f), 0x1.fffffep-1f);
-        const float y = __fadd_rz(xc, 1.0f);
-        return (int)((__float_as_uint(y) & 0x7fffffu) >> (23 - lshift));
+        const float y = __fmaf_rz(__saturatef(x), (float)(1 << lshift), 0x1p23f);
+        return (int)(__float_as_uint(y) & 0x7fffffu);
     }
 };
 
@@ -243,7 +251,7 @@ template <typename T>
 __host__ __device__ constexpr BlkLayout make_layout_c(int d, int n)
 {
     const int per16 = 16 / (int)sizeof(T);
-    const int es = round_up(n + 1, per16), dn = round_up(n, per16);
+    const int es = round_up(n + 1, per16), dn = round_up(n + 1, per16);
     const int ls = ceil_log2(n) + 1 < 2 ? 2 : ceil_log2(n) + 1;
     const int ts = round_up((1 << ls) + 2, 16);
     const int h = (int)sizeof(ChanHdr<T>);
@@ -274,7 +282,8 @@ struct Shape {
 };
 
 // Largest j in [0, n-1] with e[j] <= x (the oracle's bin rule), starting at
-// the table entry of x's cell; no step passes the last bin of the row.
+// the table entry of x's cell.  A point at or past ξ_n = 1 may return n,
+// whose density entry repeats bin n-1's.
 template <typename T, class SH>
 __device__ __forceinline__ int lookup(const SH& sh, const unsigned char* row, int span, T x)
 {
@@ -283,7 +292,7 @@ __device__ __forceinline__ int lookup(const SH& sh, const unsigned char* row, in
     int j = row[sh.tab_off() + q];
     const int nm1 = sh.n() - 1;
     if (span <= 1) {
-        if (j < nm1 && Prec<T>::le(e[j + 1], x)) j += 1;
+        j += Prec<T>::le(e[j + 1], x) ? 1 : 0;
     } else {
         for (int s = 1 << (31 - __clz(span)); s > 0; s >>= 1) {
             const int t = j + s;
@@ -339,13 +348,13 @@ __device__ __forceinline__ void forward_call(const Params& P, const SH& sh, int 
                     const T mass = __ldg(sp + SP_M), G = __ldg(sp + SP_G), A_ = __ldg(sp + SP_A);
                     p[k] = mass + G * Prec<T>::tan_(A_ * x[k] - __ldg(sp + SP_T0));
                     const T dp = p[k] - mass;
-                    J *= __ldg(sp + SP_GINVA) / (dp * dp + __ldg(sp + SP_G2));
+                    J *= Prec<T>::div(__ldg(sp + SP_GINVA), dp * dp + __ldg(sp + SP_G2));
                 } else if (kind == MAP_POW) {
                     const T x2 = x[k] * x[k], x4 = x2 * x2;
                     T pk = x4 * x[k];
                     if (pk < Prec<T>::tiny()) pk = Prec<T>::tiny();
                     p[k] = pk;
-                    J *= T(1) / (T(5) * x4);
+                    J *= Prec<T>::div(T(1), T(5) * x4);
                 }
             }
             const T u = p[k] - gc;
@@ -393,7 +402,7 @@ __device__ __forceinline__ void channel_body(const Params& P, const SH& sh, cons
 #pragma unroll
                     for (int q = 0; q < CPT; ++q) {
                         const T dp = p[q][k] - mass;
-                        const T jfac = GinvA / (dp * dp + G2);
+                        const T jfac = Prec<T>::div(GinvA, dp * dp + G2);
                         J[q] *= jfac;
                         F[q] *= jfac;
                         xk[q] = (Prec<T>::atan_(dp * invG) + t0) * invA;
@@ -406,7 +415,7 @@ __device__ __forceinline__ void channel_body(const Params& P, const SH& sh, cons
                     for (int q = 0; q < CPT; ++q) {
                         const T xx = Prec<T>::pow02(p[q][k]);
                         const T x2 = xx * xx;
-                        J[q] *= T(1) / (T(5) * (x2 * x2));
+                        J[q] *= Prec<T>::div(T(1), T(5) * (x2 * x2));
                         xk[q] = xx;
                         if (with_f) F[q] *= Prec<T>::powm08(p[q][k] + del) * ipn;
                         const T u = p[q][k] - gc;
@@ -421,7 +430,7 @@ __device__ __forceinline__ void channel_body(const Params& P, const SH& sh, cons
 #pragma unroll
                 for (int q = 0; q < CPT; ++q) {
                     const int j = lookup<T>(sh, row, sp, xk[q]);
-                    if (REC && q == 0) bins[k] = j;
+                    if (REC && q == 0) bins[k] = min(j, sh.n() - 1);
                     gp[q] *= dn[j];
                 }
             }

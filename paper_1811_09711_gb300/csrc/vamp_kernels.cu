@@ -136,7 +136,8 @@ __device__ __forceinline__ void derive_row_t(const Params& P, const BlkLayout& L
     unsigned char* tb = r + (L.Es + L.Dn) * sizeof(T);
     for (int j = lane; j <= n; j += nl) {
         e[j] = (T)e64[j];
-        if (j < n) dnr[j] = (T)(1.0 / ((double)n * (e64[j + 1] - e64[j])));
+        const int jb = j < n ? j : n - 1;  // entry n repeats bin n-1
+        dnr[j] = (T)(1.0 / ((double)n * (e64[jb + 1] - e64[jb])));
     }
     __syncwarp();
     // tb[q] = largest j in [0, n-1] with e[j] <= q/L, for q = 0..L
