@@ -213,10 +213,11 @@ vamp_status vamp_kernel_stats(vamp_ctx *ctx, double *sample_ms, int64_t *sample_
 
 /* The pass-kernel variant the context uses (chosen at create time by timing
  * the candidates once per process and shape class): FP32-eval or FP64, calls
- * per thread, and the (d, n) it is specialised for (0, 0 = any shape).  For
- * benchmarks and profiles.  Any pointer may be NULL. */
+ * per thread, the (d, n) it is specialised for (0, 0 = any shape) and the
+ * CTAs per SM it is compiled for.  For benchmarks and profiles.  Any pointer
+ * may be NULL. */
 vamp_status vamp_pass_kernel_info(const vamp_ctx *ctx, int32_t *fp32, int32_t *calls_per_thread,
-                                  int32_t *shape_d, int32_t *shape_n);
+                                  int32_t *shape_d, int32_t *shape_n, int32_t *ctas_per_sm);
 
 /* ---- many independent integrations in one launch --------------------------
  * A batch advances n integrations of possibly different d, K, n, calls and

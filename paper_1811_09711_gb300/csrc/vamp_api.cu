@@ -34,6 +34,7 @@ struct vamp_ctx {
     size_t smem_pass = 0;      // dynamic shared memory of the integration pass kernel
     size_t smem_gen = 0;       // ... of the generation pass kernel
     const PassVariant* var = nullptr;  // pass kernels in use
+    int tuned = 0;             // var was chosen by timing (first sampling pass)
     int grid_pass = 0;         // persistent grid of the integration pass kernel
     int grid_gen = 0;          // resident CTAs of the generation pass kernel
     int have_pass = 0;
@@ -121,27 +122,64 @@ vamp::PassArgs pass_args(const vamp_ctx* c, uint32_t field)
     return A;
 }
 
-// Autotuner: the fastest pass-kernel variant for a shape class, measured
-// once per process on a short integration pass and then reused.
+// Autotuner: the fastest pass-kernel variant for a shape class and call
+// count (power-of-two class), measured once per process on a pass of the
+// context's first call count and then reused.
 std::mutex g_tune_mu;
 std::map<std::tuple<int, int, int, int, int, int>, const PassVariant*> g_tuned;
 
-vamp_status choose_variant(vamp_ctx* c)
+// Tile and shared memory of one candidate (its CTAs-per-SM budget).
+struct VariantShape {
+    int tile;
+    size_t smem_pass, smem_gen;
+};
+
+VariantShape shape_of(const vamp_ctx* c, const PassVariant* v)
+{
+    VariantShape s{};
+    vamp::pass_smem_for(c->prm, c->fp32, v->minb, &s.tile, &s.smem_pass, &s.smem_gen);
+    return s;
+}
+
+// Makes v the context's pass kernel: its tile, shared memory and grids.
+vamp_status use_variant(vamp_ctx* c, const PassVariant* v)
+{
+    const VariantShape s = shape_of(c, v);
+    VAMP_CK(c, vamp::ensure_smem(v->fn[0], s.smem_pass));
+    VAMP_CK(c, vamp::ensure_smem(v->fn[1], s.smem_gen));
+    int b0 = 0, b1 = 0;
+    VAMP_CK(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b0, v->fn[0], vamp::PASS_THREADS, s.smem_pass));
+    VAMP_CK(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, v->fn[1], vamp::PASS_THREADS, s.smem_gen));
+    c->var = v;
+    c->tile = s.tile;
+    c->smem_pass = s.smem_pass;
+    c->smem_gen = s.smem_gen;
+    c->grid_pass = (b0 > 0 ? b0 : 1) * c->sm_count;
+    c->grid_gen = (b1 > 0 ? b1 : 1) * c->sm_count;
+    return VAMP_OK;
+}
+
+vamp_status choose_variant(vamp_ctx* c, int64_t n_calls)
 {
     const std::vector<const PassVariant*> cand = vamp::pass_candidates(c->fp32, c->d, c->n);
     if (cand.empty()) return fail(c, VAMP_ERR_INVALID_ARG, "no pass kernel for this shape");
     for (const PassVariant* v : cand) {
-        VAMP_CK(c, vamp::ensure_smem(v->fn[0], c->smem_pass));
-        VAMP_CK(c, vamp::ensure_smem(v->fn[1], c->smem_gen));
+        const VariantShape s = shape_of(c, v);
+        VAMP_CK(c, vamp::ensure_smem(v->fn[0], s.smem_pass));
+        VAMP_CK(c, vamp::ensure_smem(v->fn[1], s.smem_gen));
     }
     auto grid_of = [&](const PassVariant* v, int mode, int* grid) -> cudaError_t {
+        const VariantShape s = shape_of(c, v);
         int b = 0;
         cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, v->fn[mode], vamp::PASS_THREADS,
-                                                                      mode ? c->smem_gen : c->smem_pass);
+                                                                      mode ? s.smem_gen : s.smem_pass);
         *grid = (b > 0 ? b : 1) * c->sm_count;
         return e;
     };
-    const auto key = std::make_tuple(c->dev, c->fp32, c->d, c->n, std::min(c->K, 64), c->tile);
+    const int64_t probe = std::min<int64_t>(std::max<int64_t>(n_calls, 1 << 16), 1 << 24);
+    int nclass = 0;
+    while ((int64_t(1) << (nclass + 1)) <= probe) ++nclass;
+    const auto key = std::make_tuple(c->dev, c->fp32, c->d, c->n, std::min(c->K, 64), nclass);
     const PassVariant* best = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -150,9 +188,9 @@ vamp_status choose_variant(vamp_ctx* c)
     }
     if (!best && cand.size() == 1) best = cand[0];
     if (!best) {
-        // time each candidate on a short pass over the initial grids; the
-        // pass result is discarded (no finish kernel runs, state is unchanged)
-        const int64_t probe = std::max<int64_t>(1 << 18, (int64_t)c->K * 2048);
+        // time each candidate on a pass of `probe` calls over the current
+        // grids; the pass result is discarded (no finish kernel runs) and
+        // the accumulators are cleared again below
         cudaEvent_t e0, e1;
         VAMP_CK(c, cudaEventCreate(&e0));
         VAMP_CK(c, cudaEventCreate(&e1));
@@ -160,11 +198,15 @@ vamp_status choose_variant(vamp_ctx* c)
         for (const PassVariant* v : cand) {
             int grid = 0;
             VAMP_CK(c, grid_of(v, 0, &grid));
+            const VariantShape s = shape_of(c, v);
+            vamp::PassArgs A = pass_args(c, 0x7fffffffu);
+            A.tile = s.tile;
+            A.ntiles = (c->K + s.tile - 1) / s.tile;
             float ms_v = 0.f;
             for (int rep = 0; rep < 2; ++rep) {
                 VAMP_CK(c, vamp::launch_begin_pass(c->prm, probe, c->stream));
                 VAMP_CK(c, cudaEventRecord(e0, c->stream));
-                VAMP_CK(c, v->launch(c->prm, 0, pass_args(c, 0x7fffffffu), grid, c->smem_pass, c->stream));
+                VAMP_CK(c, v->launch(c->prm, 0, A, grid, s.smem_pass, c->stream));
                 VAMP_CK(c, cudaEventRecord(e1, c->stream));
                 VAMP_CK(c, cudaEventSynchronize(e1));
                 VAMP_CK(c, cudaEventElapsedTime(&ms_v, e0, e1));
@@ -173,7 +215,8 @@ vamp_status choose_variant(vamp_ctx* c)
         }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
-        // the probe touched the accumulators and scalars: clear them
+        // the probe touched the accumulators and the pass scalars (not the
+        // combination history: tuning runs before the first pass)
         VAMP_CK(c, cudaMemsetAsync(c->prm.D, 0, (size_t)c->K * c->d * c->n * 8, c->stream));
         VAMP_CK(c, cudaMemsetAsync(c->prm.csum, 0, (size_t)2 * c->K * 8, c->stream));
         VAMP_CK(c, cudaMemsetAsync(c->prm.sc, 0, HEAD_BYTES, c->stream));
@@ -181,10 +224,7 @@ vamp_status choose_variant(vamp_ctx* c)
         std::lock_guard<std::mutex> lk(g_tune_mu);
         g_tuned[key] = best;
     }
-    c->var = best;
-    VAMP_CK(c, grid_of(best, 0, &c->grid_pass));
-    VAMP_CK(c, grid_of(best, 1, &c->grid_gen));
-    return VAMP_OK;
+    return use_variant(c, best);
 }
 
 }  // namespace
@@ -279,7 +319,11 @@ vamp_status vamp_create(const vamp_config* cfg, void* cuda_stream, vamp_ctx** ou
         CREATE_CK(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->dev));
         if ((int)c->smem_pass > maxsm) { st = fail(c, VAMP_ERR_INVALID_ARG, "grid too large for shared memory"); goto create_fail; }
         CREATE_CK(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->dev));
-        st = choose_variant(c);
+        // until the first pass picks by timing: the first candidate (the
+        // shape-specialised kernel if there is one)
+        const std::vector<const PassVariant*> cand = vamp::pass_candidates(c->fp32, c->d, c->n);
+        if (cand.empty()) { st = fail(c, VAMP_ERR_INVALID_ARG, "no pass kernel for this shape"); goto create_fail; }
+        st = use_variant(c, cand[0]);
         if (st != VAMP_OK) goto create_fail;
     }
 #undef CREATE_CK
@@ -312,6 +356,11 @@ vamp_status vamp_sample_pass(vamp_ctx* c, int64_t n_calls, uint32_t iteration, v
     if (n_calls + (int64_t)c->K * c->prm.n_min > int64_t(0xffffffff))
         return fail(c, VAMP_ERR_INVALID_ARG, "too many calls for a 32-bit call counter");
     DeviceGuard g(c->dev);
+    if (!c->tuned) {
+        const vamp_status ts = choose_variant(c, n_calls);
+        if (ts != VAMP_OK) return ts;
+        c->tuned = 1;
+    }
     const Params& P = c->prm;
     VAMP_CK(c, cudaMemsetAsync(P.D, 0, (size_t)c->K * c->d * c->n * 8, c->stream));
     VAMP_CK(c, cudaMemsetAsync(P.csum, 0, (size_t)2 * c->K * 8, c->stream));
@@ -557,13 +606,14 @@ vamp_status vamp_kernel_stats(vamp_ctx* c, double* sample_ms, int64_t* sample_la
 }
 
 vamp_status vamp_pass_kernel_info(const vamp_ctx* c, int32_t* fp32, int32_t* cpt, int32_t* shape_d,
-                                  int32_t* shape_n)
+                                  int32_t* shape_n, int32_t* ctas_per_sm)
 {
     if (!c || !c->var) return VAMP_ERR_INVALID_ARG;
     if (fp32) *fp32 = c->var->fp32;
     if (cpt) *cpt = c->var->cpt;
     if (shape_d) *shape_d = c->var->D;
     if (shape_n) *shape_n = c->var->NB;
+    if (ctas_per_sm) *ctas_per_sm = c->var->minb;
     return VAMP_OK;
 }
 

@@ -19,6 +19,7 @@
 // with the last bin's density.
 #pragma once
 
+#include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -61,9 +62,11 @@ struct ChanHdr {
     uint32_t kinds;      // byte s: map kind of slot s
     uint64_t slotpack;   // 4 bits per coordinate: its slot
     T wz;                // matching peak: weight x Z^-(d - nmap)
-    T pad[16 / sizeof(T) - 1];
+    uint32_t slow;       // bit k: some cell of row k overlaps more than two bins (kept by the derive kernel)
+    uint32_t pad[(16 - (sizeof(T) + 4) % 16) % 16 / 4];
     T sp[MAXMAP][SP_N];  // per slot: m, Γ, A, Γ², 1/Γ, Γ/A, 1/A, atan(m/Γ), δ, 1/powN
 };
+static_assert(sizeof(ChanHdr<float>) % 16 == 0 && sizeof(ChanHdr<double>) % 16 == 0, "header not 16-byte sized");
 
 // Byte layout of one channel's lookup block for element type T.
 struct BlkLayout {
@@ -236,7 +239,7 @@ template <> struct Prec<float> {
     static __device__ __forceinline__ int cell(float x, int lshift)
     {
         const float y = __fmaf_rz(__saturatef(x), (float)(1 << lshift), 0x1p23f);
-        return (int)(__float_as_uint(y) & 0x7fffffu);
+        return (int)(__float_as_uint(y) - 0x4B000000u);  // y - 2^23 (bit pattern of 2^23 is 0x4B000000)
     }
 };
 
@@ -280,6 +283,16 @@ struct Shape {
         return blk + H() + k * R();
     }
 };
+
+// Bin of x in a row whose cells overlap at most two bins: the cell's table
+// entry, plus one if x reaches the next edge.
+template <typename T, class SH>
+__device__ __forceinline__ int lookup_fast(const SH& sh, const unsigned char* row, T x)
+{
+    const T* e = reinterpret_cast<const T*>(row);
+    const int j = row[sh.tab_off() + Prec<T>::cell(x, sh.lshift())];
+    return j + (Prec<T>::le(e[j + 1], x) ? 1 : 0);
+}
 
 // Largest j in [0, n-1] with e[j] <= x (the oracle's bin rule), starting at
 // the table entry of x's cell.  A point at or past ξ_n = 1 may return n,
@@ -372,20 +385,21 @@ __device__ __forceinline__ void forward_call(const Params& P, const SH& sh, int 
 //   f_q += wz_c' 2^-(A_q - Σ_mapped a_k) Π_mapped factor(p_k)
 // REC records the bin indices of call 0 into bins[0..d-1].
 // ---------------------------------------------------------------------------
-template <typename T, int CPT, bool REC, class SH>
-__device__ __forceinline__ void channel_body(const Params& P, const SH& sh, const unsigned char* blk, T alpha_c,
-                                             bool lookups, bool with_f, const T (&p)[CPT][SH::DM],
-                                             const T (&A)[CPT], const bool (&skip)[CPT], T (&g)[CPT],
-                                             T (&f)[CPT], int* bins)
+// Rows of one channel against CPT calls: bin densities (gp), Jacobians of the
+// mapped coordinates (J), matching-peak factors (F) and Gaussian exponents of
+// the mapped coordinates (as).  FAST: every row's cells overlap at most two
+// bins, so one edge probe settles each bin and the unrolled row loop has no
+// branch other than the mapped-coordinate test.
+template <typename T, int CPT, bool REC, bool FAST, class SH>
+__device__ __forceinline__ void channel_rows(const Params& P, const SH& sh, const unsigned char* blk, bool with_f,
+                                             const T (&p)[CPT][SH::DM], T (&J)[CPT], T (&F)[CPT], T (&gp)[CPT],
+                                             T (&as)[CPT], int* bins)
 {
     const int d = sh.d();
     const ChanHdr<T>& h = *reinterpret_cast<const ChanHdr<T>*>(blk);
     const uint32_t mask = h.mask, kinds = h.kinds;
     const uint64_t slotpack = h.slotpack;
     const T gc = Prec<T>::gcen(P), k2 = Prec<T>::gk2(P);
-    T J[CPT], F[CPT], gp[CPT], as[CPT];
-#pragma unroll
-    for (int q = 0; q < CPT; ++q) { J[q] = T(1); F[q] = T(1); gp[q] = T(1); as[q] = T(0); }
 #pragma unroll
     for (int k = 0; k < SH::DM; ++k) {
         if (k < d) {
@@ -423,9 +437,18 @@ __device__ __forceinline__ void channel_body(const Params& P, const SH& sh, cons
                     }
                 }
             }
-            if (lookups) {
-                const unsigned char* row = sh.row(blk, k);
-                const T* dn = reinterpret_cast<const T*>(row + sh.dens_off());
+            // every channel's rows are probed; the terms of the own channel
+            // and of switched-off channels are dropped by the caller
+            const unsigned char* row = sh.row(blk, k);
+            const T* dn = reinterpret_cast<const T*>(row + sh.dens_off());
+            if (FAST) {
+#pragma unroll
+                for (int q = 0; q < CPT; ++q) {
+                    const int j = lookup_fast<T>(sh, row, xk[q]);
+                    if (REC && q == 0) bins[k] = min(j, sh.n() - 1);
+                    gp[q] *= dn[j];
+                }
+            } else {
                 const int sp = row[sh.tab_off() + (1 << sh.lshift()) + 1];
 #pragma unroll
                 for (int q = 0; q < CPT; ++q) {
@@ -436,6 +459,20 @@ __device__ __forceinline__ void channel_body(const Params& P, const SH& sh, cons
             }
         }
     }
+}
+
+template <typename T, int CPT, bool REC, class SH>
+__device__ __forceinline__ void channel_body(const Params& P, const SH& sh, const unsigned char* blk, T alpha_c,
+                                             bool lookups, bool with_f, const T (&p)[CPT][SH::DM],
+                                             const T (&A)[CPT], const bool (&skip)[CPT], T (&g)[CPT],
+                                             T (&f)[CPT], int* bins)
+{
+    const ChanHdr<T>& h = *reinterpret_cast<const ChanHdr<T>*>(blk);
+    T J[CPT], F[CPT], gp[CPT], as[CPT];
+#pragma unroll
+    for (int q = 0; q < CPT; ++q) { J[q] = T(1); F[q] = T(1); gp[q] = T(1); as[q] = T(0); }
+    if (h.slow == 0u) channel_rows<T, CPT, REC, true>(P, sh, blk, with_f, p, J, F, gp, as, bins);
+    else channel_rows<T, CPT, REC, false>(P, sh, blk, with_f, p, J, F, gp, as, bins);
     const T wz = h.wz;
 #pragma unroll
     for (int q = 0; q < CPT; ++q) {

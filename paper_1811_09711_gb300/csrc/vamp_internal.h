@@ -54,6 +54,7 @@ struct EvalArgs {
 // per thread, and the shape it is specialised for (D = NB = 0: any shape).
 struct PassVariant {
     int fp32, cpt, D, NB;
+    int minb;  // CTAs per SM the kernel is compiled for (register cap), sizes its tile budget
     const void* fn[2];
     cudaError_t (*launch)(const Params& P, int mode, const PassArgs& A, int grid, size_t smem, cudaStream_t s);
 };
@@ -84,8 +85,10 @@ void bind_arena(Params& P, unsigned char* base, const Arena& A);  // sets every 
 // Copies headers and peak records into the arena (async on s).
 cudaError_t upload_setup(const Params& P, const Setup& S, cudaStream_t s);
 
-// Tile and shared-memory size of the pass kernel for element size esz.
+// Tile and shared-memory size of the pass kernel: two CTAs per SM
+// (TILE_BUDGET), or `minb` CTAs per SM of the current device.
 void pass_smem(const Params& P, int fp32, int* tile, size_t* smem_int, size_t* smem_gen);
+void pass_smem_for(const Params& P, int fp32, int minb, int* tile, size_t* smem_int, size_t* smem_gen);
 // Candidate kernels for a shape: exact (D, NB) matches first, then generic.
 std::vector<const PassVariant*> pass_candidates(int fp32, int d, int n);
 // Raises (never lowers) the dynamic shared-memory limit of a kernel.

@@ -156,7 +156,13 @@ __device__ __forceinline__ void derive_row_t(const Params& P, const BlkLayout& L
     for (int q = lane; q < Lc; q += nl) span = max(span, (int)tb[q + 1] - (int)tb[q]);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) span = max(span, __shfl_xor_sync(0xffffffffu, span, o));
-    if (lane == 0) tb[Lc + 1] = (unsigned char)min(span, 255);
+    if (lane == 0) {
+        tb[Lc + 1] = (unsigned char)min(span, 255);
+        // this row's bit of the channel's slow-row mask (each row owns its bit)
+        unsigned int* slow = reinterpret_cast<unsigned int*>(lk + (size_t)c * L.bytes + offsetof(ChanHdr<T>, slow));
+        if (span > 1) atomicOr(slow, 1u << k);
+        else atomicAnd(slow, ~(1u << k));
+    }
 }
 
 __device__ __forceinline__ void derive_row(const Params& P, int row, int lane)

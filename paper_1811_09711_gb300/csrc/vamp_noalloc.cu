@@ -99,8 +99,8 @@ extern "C" vamp_status vamp_sample_pass_static(const vamp_config* cfg, const dou
     }
     int tile = 1;
     size_t smem = 0, smem_gen = 0;
-    vamp::pass_smem(pr, fp32, &tile, &smem, &smem_gen);
     const std::vector<const vamp::PassVariant*> cand = vamp::pass_candidates(fp32, d, n);
+    vamp::pass_smem_for(pr, fp32, cand.empty() ? 2 : cand[0]->minb, &tile, &smem, &smem_gen);
 
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);

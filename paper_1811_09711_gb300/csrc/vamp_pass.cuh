@@ -185,8 +185,8 @@ __device__ __forceinline__ void block_max_to(SmemHead& H, double wm, unsigned lo
     }
 }
 
-template <typename T, int MODE, int CPT, int D_, int NB_>
-__global__ void __launch_bounds__(PASS_THREADS, 2) k_pass(Params P, PassArgs A)
+template <typename T, int MODE, int CPT, int D_, int NB_, int MINB>
+__global__ void __launch_bounds__(PASS_THREADS, MINB) k_pass(Params P, PassArgs A)
 {
     using SH = Shape<T, D_, NB_>;
     constexpr int DM = SH::DM;
@@ -368,16 +368,17 @@ drain:
     __syncthreads();
 }
 
-// Registers the integration and generation kernels of one (T, CPT, D, NB).
-template <typename T, int CPT, int D_, int NB_>
+// Registers the integration and generation kernels of one (T, CPT, D, NB,
+// CTAs per SM).
+template <typename T, int CPT, int D_, int NB_, int MINB>
 cudaError_t pass_launch_t(const Params& P, int mode, const PassArgs& A, int grid, size_t smem, cudaStream_t s)
 {
-    if (mode) k_pass<T, 1, CPT, D_, NB_><<<grid, PASS_THREADS, smem, s>>>(P, A);
-    else k_pass<T, 0, CPT, D_, NB_><<<grid, PASS_THREADS, smem, s>>>(P, A);
+    if (mode) k_pass<T, 1, CPT, D_, NB_, MINB><<<grid, PASS_THREADS, smem, s>>>(P, A);
+    else k_pass<T, 0, CPT, D_, NB_, MINB><<<grid, PASS_THREADS, smem, s>>>(P, A);
     return cudaGetLastError();
 }
 
-template <typename T, int CPT, int D_, int NB_>
+template <typename T, int CPT, int D_, int NB_, int MINB = 2>
 PassVariant make_variant()
 {
     PassVariant v;
@@ -385,9 +386,10 @@ PassVariant make_variant()
     v.cpt = CPT;
     v.D = D_;
     v.NB = NB_;
-    v.fn[0] = (const void*)k_pass<T, 0, CPT, D_, NB_>;
-    v.fn[1] = (const void*)k_pass<T, 1, CPT, D_, NB_>;
-    v.launch = &pass_launch_t<T, CPT, D_, NB_>;
+    v.minb = MINB;
+    v.fn[0] = (const void*)k_pass<T, 0, CPT, D_, NB_, MINB>;
+    v.fn[1] = (const void*)k_pass<T, 1, CPT, D_, NB_, MINB>;
+    v.launch = &pass_launch_t<T, CPT, D_, NB_, MINB>;
     return v;
 }
 

@@ -8,6 +8,9 @@ void add_pass_variants_f32_shapes(std::vector<PassVariant>& v)
 {
     v.push_back(make_variant<float, 2, 14, 100>());
     v.push_back(make_variant<float, 4, 14, 100>());
+    v.push_back(make_variant<float, 1, 14, 100, 3>());
+    v.push_back(make_variant<float, 2, 14, 100, 3>());
+    v.push_back(make_variant<float, 1, 14, 100, 4>());
     v.push_back(make_variant<float, 4, 8, 50>());
     v.push_back(make_variant<float, 4, 4, 20>());
 }

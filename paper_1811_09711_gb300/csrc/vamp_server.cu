@@ -188,7 +188,7 @@ vamp_status admit(vamp_server* s, Req* r)
     if (e == cudaSuccess) e = cudaStreamSynchronize(r->stream);
     if (e != cudaSuccess) return VAMP_ERR_CUDA;
     // generation kernel of this shape
-    vamp::pass_smem(P, s->fp32, &r->tile, &r->smem_int, &r->smem_gen);
+    vamp::pass_smem_for(P, s->fp32, r->var->minb, &r->tile, &r->smem_int, &r->smem_gen);
     e = vamp::ensure_smem(r->var->fn[1], r->smem_gen);
     int bps = 0;
     if (e == cudaSuccess)

@@ -247,16 +247,35 @@ cudaError_t upload_setup(const Params& P, const Setup& S, cudaStream_t s)
     return e;
 }
 
-void pass_smem(const Params& P, int fp32, int* tile, size_t* smem_int, size_t* smem_gen)
+namespace {
+void smem_for_budget(const Params& P, int fp32, size_t budget, int* tile, size_t* smem_int, size_t* smem_gen)
 {
     const size_t S = (size_t)(fp32 ? P.lay32.bytes : P.lay64.bytes);
     const size_t ds = (size_t)P.d * P.n * 8;
-    long t = (long)((TILE_BUDGET - SMEM_HEAD - ds) / (2 * S));
+    long t = budget > SMEM_HEAD + ds ? (long)((budget - SMEM_HEAD - ds) / (2 * S)) : 1;
     if (t < 1) t = 1;
     if (t > P.K) t = P.K;
     *tile = (int)t;
     *smem_int = SMEM_HEAD + 2 * (size_t)t * S + ds;
     *smem_gen = SMEM_HEAD + 2 * (size_t)t * S;
+}
+}  // namespace
+
+void pass_smem(const Params& P, int fp32, int* tile, size_t* smem_int, size_t* smem_gen)
+{
+    smem_for_budget(P, fp32, TILE_BUDGET, tile, smem_int, smem_gen);
+}
+
+void pass_smem_for(const Params& P, int fp32, int minb, int* tile, size_t* smem_int, size_t* smem_gen)
+{
+    // per-CTA share of the SM's shared memory, less the per-CTA reservation
+    int dev = 0, per_sm = 0, reserved = 0;
+    size_t budget = TILE_BUDGET;
+    if (minb > 2 && cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) == cudaSuccess)
+        budget = std::min(budget, (size_t)(per_sm / minb - reserved));
+    smem_for_budget(P, fp32, budget, tile, smem_int, smem_gen);
 }
 
 std::vector<const PassVariant*> pass_candidates(int fp32, int d, int n)

@@ -116,7 +116,7 @@ def load():
                                                 C.POINTER(PassResult), C.c_char_p, i32]
         lib.vamp_sample_pass_static.restype = st
         lib.vamp_pass_kernel_info.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32),
-                                              C.POINTER(i32)]
+                                                C.POINTER(i32), C.POINTER(i32)]
         lib.vamp_pass_kernel_info.restype = st
         lib.vamp_batch_create.argtypes = [C.POINTER(Config), i32, i32, C.POINTER(vp)]
         lib.vamp_batch_create.restype = st
@@ -277,15 +277,18 @@ class Vamp:
                 "gen_launches": gn.value}
 
     def kernel_info(self):
-        f, c, dd, nn = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
-        self._check(self.lib.vamp_pass_kernel_info(self.h, C.byref(f), C.byref(c), C.byref(dd), C.byref(nn)))
-        return {"fp32": f.value, "calls_per_thread": c.value, "shape_d": dd.value, "shape_n": nn.value}
+        f, c, dd, nn, mb = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
+        self._check(self.lib.vamp_pass_kernel_info(self.h, C.byref(f), C.byref(c), C.byref(dd), C.byref(nn),
+                                                   C.byref(mb)))
+        return {"fp32": f.value, "calls_per_thread": c.value, "shape_d": dd.value, "shape_n": nn.value,
+                "ctas_per_sm": mb.value}
 
     def kernel_name(self, mode: int = 0) -> str:
         """Name of the pass kernel as profilers print it."""
         k = self.kernel_info()
         t = "float" if k["fp32"] else "double"
-        return f"k_pass<{t}, {mode}, {k['calls_per_thread']}, {k['shape_d']}, {k['shape_n']}>"
+        return (f"k_pass<{t}, {mode}, {k['calls_per_thread']}, {k['shape_d']}, {k['shape_n']}, "
+                f"{k['ctas_per_sm']}>")
 
     # -- state ---------------------------------------------------------------
     def get_state(self):
