@@ -226,9 +226,18 @@ template <> struct Prec<float> {
     static __device__ __forceinline__ float lerp(float e0, float e1, float fr) { return fmaf(fr, e1 - e0, e0); }
     static __device__ __forceinline__ float tan_(float v) { return tanf(v); }
     static __device__ __forceinline__ float atan_(float v) { return atanf(v); }
-    static __device__ __forceinline__ float pow02(float v) { return exp2f(0.2f * __log2f(v)); }
-    static __device__ __forceinline__ float powm08(float v) { return exp2f(-0.8f * __log2f(v)); }
-    static __device__ __forceinline__ float exp2_(float v) { return exp2f(v); }
+    // 2^v by the ex2.approx instruction (relative error about 2^-22; flushes
+    // results below the normal range to zero, where the factors it scales
+    // are negligible)
+    static __device__ __forceinline__ float ex2(float v)
+    {
+        float r;
+        asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+        return r;
+    }
+    static __device__ __forceinline__ float pow02(float v) { return ex2(0.2f * __log2f(v)); }
+    static __device__ __forceinline__ float powm08(float v) { return ex2(-0.8f * __log2f(v)); }
+    static __device__ __forceinline__ float exp2_(float v) { return ex2(v); }
     // Jacobian factors of the FP32-eval form: reciprocal-based quotient
     // (within 2 ulp for the normal denominators that occur here)
     static __device__ __forceinline__ float div(float a, float b) { return __fdividef(a, b); }
@@ -389,7 +398,8 @@ __device__ __forceinline__ void forward_call(const Params& P, const SH& sh, int 
 // mapped coordinates (J), matching-peak factors (F) and Gaussian exponents of
 // the mapped coordinates (as).  FAST: every row's cells overlap at most two
 // bins, so one edge probe settles each bin and the unrolled row loop has no
-// branch other than the mapped-coordinate test.
+// branch other than the mapped-coordinate test; otherwise rows are tested
+// one by one and only the spanning ones search.
 template <typename T, int CPT, bool REC, bool FAST, class SH>
 __device__ __forceinline__ void channel_rows(const Params& P, const SH& sh, const unsigned char* blk, bool with_f,
                                              const T (&p)[CPT][SH::DM], T (&J)[CPT], T (&F)[CPT], T (&gp)[CPT],
@@ -397,7 +407,7 @@ __device__ __forceinline__ void channel_rows(const Params& P, const SH& sh, cons
 {
     const int d = sh.d();
     const ChanHdr<T>& h = *reinterpret_cast<const ChanHdr<T>*>(blk);
-    const uint32_t mask = h.mask, kinds = h.kinds;
+    const uint32_t mask = h.mask, kinds = h.kinds, slow = h.slow;
     const uint64_t slotpack = h.slotpack;
     const T gc = Prec<T>::gcen(P), k2 = Prec<T>::gk2(P);
 #pragma unroll
@@ -442,6 +452,13 @@ __device__ __forceinline__ void channel_rows(const Params& P, const SH& sh, cons
             const unsigned char* row = sh.row(blk, k);
             const T* dn = reinterpret_cast<const T*>(row + sh.dens_off());
             if (FAST) {
+#pragma unroll
+                for (int q = 0; q < CPT; ++q) {
+                    const int j = lookup_fast<T>(sh, row, xk[q]);
+                    if (REC && q == 0) bins[k] = min(j, sh.n() - 1);
+                    gp[q] *= dn[j];
+                }
+            } else if (!((slow >> k) & 1u)) {
 #pragma unroll
                 for (int q = 0; q < CPT; ++q) {
                     const int j = lookup_fast<T>(sh, row, xk[q]);
