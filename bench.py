@@ -475,7 +475,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--batch-iters", type=int, default=3, help="timed iterations of the 256-instance batch (0: skip)")
     ap.add_argument("--serve-seconds", type=float, default=60.0, help="arrival window of the request stream (0: skip)")
-    ap.add_argument("--serve-seconds-fp64", type=float, default=2.0, help="arrival window for the FP64 form")
+    ap.add_argument("--serve-seconds-fp64", type=float, default=1.0, help="arrival window for the FP64 form")
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-slots", type=int, default=256)
     args = ap.parse_args()

@@ -73,7 +73,9 @@ vamp_status bfail(vamp_batch* b, vamp_status s, const std::string& msg)
 
 size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
 
-int calls_per_thread(int fp32) { return fp32 ? 1 : 1; }
+// Calls per thread of the multi-instance kernel's small-d classes: work
+// items are sized in multiples of PASS_THREADS times this.
+int calls_per_thread(int) { return 2; }
 
 vamp::MultiArgs margs(const vamp_batch* b)
 {

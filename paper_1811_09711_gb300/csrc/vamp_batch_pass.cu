@@ -9,21 +9,114 @@
 // streams that instance's channel tiles through the two bulk-copy buffers
 // and runs the same three phases as the single-instance pass kernel.  No CTA
 // waits on another CTA: the counter is the only shared state.
+//
+// The item code is compiled for four dimension classes (d in 1..4, 5..8,
+// 9..12, 13..16): each unrolls its row loops to the class's largest d with
+// no test on the rows every member has, and the classes of small d process
+// two calls per thread.
 #include "vamp_pass.cuh"
 
 namespace vamp {
 
-template <typename T, int CPT>
+// Barrier bookkeeping of a CTA across items: use v of an item lives in
+// buffer v%2 (streaming) or v, at phase done_b + v/2 (or 0).
+struct ItemPipe {
+    uint32_t done0 = 0u, done1 = 0u;
+};
+
+// One work item: calls [a, b) of channel c of the instance in Ps.  Returns
+// false if a bounded wait gave up (the CTA then drains and exits).
+template <typename T, int CPT, class SH>
+__device__ __forceinline__ bool run_item(const MultiArgs& M, const Params& P, SmemHead& H, unsigned char* buf0,
+                                         int inst, int c, long long kth, ItemPipe& pp, bool& bad)
+{
+    constexpr int B = PASS_THREADS * CPT;
+    const int tid = threadIdx.x;
+    const SH sh(Prec<T>::lay(P), P.d, P.n);
+    const int tile = M.tiles[inst];
+    const int ntiles = (P.K + tile - 1) / tile;
+    const int S = sh.bytes();
+    const size_t tile_bytes = (size_t)tile * S;
+    double* Ds = reinterpret_cast<double*>(buf0 + 2 * tile_bytes);
+    const int dn = P.d * P.n;
+    const int64_t a = P.Pc[c] + kth * M.item_calls;
+    const int64_t b = min(a + M.item_calls, (int64_t)P.Pc[c + 1]);
+    const int64_t nb = (b - a + B - 1) / B;
+    const bool streaming = ntiles > 2;
+    const int64_t total_uses = streaming ? nb * ntiles : ntiles;
+    const unsigned char* lk = Prec<T>::lk(P);
+    auto issue = [&](int64_t u) {
+        const int t = (int)(u % ntiles);
+        const int cnt = min(tile, P.K - t * tile);
+        fence_proxy_async_smem();
+        bulk_load(buf0 + (u & 1) * tile_bytes, lk + (size_t)t * tile_bytes, (uint32_t)(cnt * S), &H.bar[u & 1]);
+    };
+    for (int q = tid; q < dn; q += PASS_THREADS) Ds[q] = 0.0;
+    __syncthreads();
+    if (tid == 0) {
+        issue(0);
+        if (total_uses > 1) issue(1);
+    }
+    int64_t u = 0, issued = total_uses > 1 ? 2 : 1;
+    double s1 = 0.0, s2 = 0.0, wm = 0.0;
+    const double sft = P.shift[c];
+    for (int64_t bt = 0; bt < nb; ++bt) {
+        const int64_t base = a + bt * B, end = min(b, base + B);
+        Calls<T, CPT, SH::DM> C;
+        phase_a<T, 0, CPT>(P, sh, M.iter[inst], base, end, c, C);
+        for (int t = 0; t < ntiles; ++t) {
+            const int bb = streaming ? (int)(u & 1) : t;
+            if (streaming || bt == 0) {
+                const uint32_t ph = (bb ? pp.done1 : pp.done0) + (streaming ? (uint32_t)(u >> 1) : 0u);
+                if (!mbar_wait_bounded(&H.bar[bb], ph & 1u)) {
+                    atomicOr(&P.sc->err, ERR_TIMEOUT);
+                    H.abort = 1;
+                }
+            }
+            if (!H.abort) tile_compute<T, 0, CPT>(P, sh, buf0 + bb * tile_bytes, t, tile, c, C);
+            __syncthreads();
+            if (H.abort) {
+                // let this CTA's copies in flight land (bounded), then give up
+                if (tid == 0) {
+                    for (int64_t v = u; v < issued; ++v) {
+                        const int vb = streaming ? (int)(v & 1) : (int)v;
+                        const uint32_t ph = (vb ? pp.done1 : pp.done0) + (streaming ? (uint32_t)(v >> 1) : 0u);
+                        mbar_wait_bounded(&H.bar[vb], ph & 1u);
+                    }
+                }
+                __syncthreads();
+                return false;
+            }
+            if (streaming && tid == 0 && issued < total_uses) {
+                issue(issued);
+                ++issued;
+            }
+            ++u;
+        }
+        phase_c_int<T, CPT>(sh, C, sft, Ds, s1, s2, wm, bad);
+    }
+    // uses of each buffer in this item
+    if (streaming) {
+        pp.done0 += (uint32_t)((total_uses + 1) / 2);
+        pp.done1 += (uint32_t)(total_uses / 2);
+    } else {
+        pp.done0 += 1u;
+        pp.done1 += ntiles > 1 ? 1u : 0u;
+    }
+    flush_segment(P, H, c, dn, Ds, s1, s2);
+    block_max_to(H, wm, &P.sc->wmax_bits);
+    return true;
+}
+
+template <typename T>
 __global__ void __launch_bounds__(PASS_THREADS, 2) k_pass_multi(MultiArgs M)
 {
-    using SH = Shape<T, 0, 0>;
     static_assert(sizeof(Params) <= PARAMS_SLOT, "Params does not fit its shared-memory slot");
     extern __shared__ __align__(128) unsigned char smem[];
     SmemHead& H = *reinterpret_cast<SmemHead*>(smem);
     Params& Ps = *reinterpret_cast<Params*>(smem + SMEM_HEAD);
     unsigned char* buf0 = smem + SMEM_HEAD + PARAMS_SLOT;
     __shared__ long long s_item;
-    constexpr int B = PASS_THREADS * CPT;
     const int tid = threadIdx.x;
     if (tid == 0) {
         mbar_init(&H.bar[0], 1);
@@ -32,9 +125,7 @@ __global__ void __launch_bounds__(PASS_THREADS, 2) k_pass_multi(MultiArgs M)
         fence_mbar_init();
     }
     __syncthreads();
-    // phases of each barrier completed before the current item: use v of an
-    // item lives in buffer v%2 (streaming) or v, at phase done_b + v/2 (or 0)
-    uint32_t done0 = 0u, done1 = 0u;
+    ItemPipe pp;
     int cur = -1;
     bool bad = false;
     for (;;) {
@@ -65,98 +156,30 @@ __global__ void __launch_bounds__(PASS_THREADS, 2) k_pass_multi(MultiArgs M)
             cur = inst;
         }
         __syncthreads();
-        const Params& P = Ps;
-        const SH sh(Prec<T>::lay(P), P.d, P.n);
-        const int tile = M.tiles[inst];
-        const int ntiles = (P.K + tile - 1) / tile;
-        const int S = sh.bytes();
-        const size_t tile_bytes = (size_t)tile * S;
-        double* Ds = reinterpret_cast<double*>(buf0 + 2 * tile_bytes);
-        const int dn = P.d * P.n;
-        const int64_t a = P.Pc[c] + kth * M.item_calls;
-        const int64_t b = min(a + M.item_calls, (int64_t)P.Pc[c + 1]);
-        const int64_t nb = (b - a + B - 1) / B;
-        const bool streaming = ntiles > 2;
-        const int64_t total_uses = streaming ? nb * ntiles : ntiles;
-        const unsigned char* lk = Prec<T>::lk(P);
-        auto issue = [&](int64_t u) {
-            const int t = (int)(u % ntiles);
-            const int cnt = min(tile, P.K - t * tile);
-            fence_proxy_async_smem();
-            bulk_load(buf0 + (u & 1) * tile_bytes, lk + (size_t)t * tile_bytes, (uint32_t)(cnt * S), &H.bar[u & 1]);
-        };
-        for (int q = tid; q < dn; q += PASS_THREADS) Ds[q] = 0.0;
-        __syncthreads();
-        if (tid == 0) {
-            issue(0);
-            if (total_uses > 1) issue(1);
-        }
-        int64_t u = 0, issued = total_uses > 1 ? 2 : 1;
-        double s1 = 0.0, s2 = 0.0, wm = 0.0;
-        const double sft = P.shift[c];
-        for (int64_t bt = 0; bt < nb; ++bt) {
-            const int64_t base = a + bt * B, end = min(b, base + B);
-            Calls<T, CPT, SH::DM> C;
-            phase_a<T, 0, CPT>(P, sh, M.iter[inst], base, end, c, C);
-            for (int t = 0; t < ntiles; ++t) {
-                const int bb = streaming ? (int)(u & 1) : t;
-                if (streaming || bt == 0) {
-                    const uint32_t ph = (bb ? done1 : done0) + (streaming ? (uint32_t)(u >> 1) : 0u);
-                    if (!mbar_wait_bounded(&H.bar[bb], ph & 1u)) {
-                        atomicOr(&P.sc->err, ERR_TIMEOUT);
-                        H.abort = 1;
-                    }
-                }
-                if (!H.abort) tile_compute<T, 0, CPT>(P, sh, buf0 + bb * tile_bytes, t, tile, c, C);
-                __syncthreads();
-                if (H.abort) goto drain;
-                if (streaming && tid == 0 && issued < total_uses) {
-                    issue(issued);
-                    ++issued;
-                }
-                ++u;
-            }
-            phase_c_int<T, CPT>(sh, C, sft, Ds, s1, s2, wm, bad);
-        }
-        // uses of each buffer in this item
-        if (streaming) {
-            done0 += (uint32_t)((total_uses + 1) / 2);
-            done1 += (uint32_t)(total_uses / 2);
-        } else {
-            done0 += 1u;
-            done1 += ntiles > 1 ? 1u : 0u;
-        }
-        flush_segment(P, H, c, dn, Ds, s1, s2);
-        block_max_to(H, wm, &P.sc->wmax_bits);
+        const int d = Ps.d;
+        bool ok;
+        if (d <= 4) ok = run_item<T, 2, Shape<T, 0, 0, 4, 1>>(M, Ps, H, buf0, inst, c, kth, pp, bad);
+        else if (d <= 8) ok = run_item<T, 2, Shape<T, 0, 0, 8, 5>>(M, Ps, H, buf0, inst, c, kth, pp, bad);
+        else if (d <= 12) ok = run_item<T, 1, Shape<T, 0, 0, 12, 9>>(M, Ps, H, buf0, inst, c, kth, pp, bad);
+        else ok = run_item<T, 1, Shape<T, 0, 0, 16, 13>>(M, Ps, H, buf0, inst, c, kth, pp, bad);
+        if (!ok) return;
         if (bad) {
-            atomicOr(&P.sc->err, ERR_NONFINITE);
+            atomicOr(&Ps.sc->err, ERR_NONFINITE);
             bad = false;
         }
         __syncthreads();
-        continue;
-    drain:
-        // a wait gave up: let this CTA's copies in flight land (bounded), then exit
-        if (tid == 0) {
-            for (int64_t v = u; v < issued; ++v) {
-                const int bb = streaming ? (int)(v & 1) : (int)v;
-                const uint32_t ph = (bb ? done1 : done0) + (streaming ? (uint32_t)(v >> 1) : 0u);
-                mbar_wait_bounded(&H.bar[bb], ph & 1u);
-            }
-        }
-        __syncthreads();
-        return;
     }
 }
 
 const void* pass_multi_kernel(int fp32)
 {
-    return fp32 ? (const void*)k_pass_multi<float, 1> : (const void*)k_pass_multi<double, 1>;
+    return fp32 ? (const void*)k_pass_multi<float> : (const void*)k_pass_multi<double>;
 }
 
 cudaError_t launch_pass_multi(int fp32, const MultiArgs& M, int grid, size_t smem, cudaStream_t s)
 {
-    if (fp32) k_pass_multi<float, 1><<<grid, PASS_THREADS, smem, s>>>(M);
-    else k_pass_multi<double, 1><<<grid, PASS_THREADS, smem, s>>>(M);
+    if (fp32) k_pass_multi<float><<<grid, PASS_THREADS, smem, s>>>(M);
+    else k_pass_multi<double><<<grid, PASS_THREADS, smem, s>>>(M);
     return cudaGetLastError();
 }
 

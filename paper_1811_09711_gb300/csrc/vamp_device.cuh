@@ -255,6 +255,8 @@ template <> struct Prec<float> {
 // ---------------------------------------------------------------------------
 // Shape policy: D_, NB_ > 0 fix the dimension and the bins at compile time
 // (all block offsets become constants); 0 means "read from the layout".
+// With D_ = 0 the dimension is only known to lie in [DLO_, DMAX_]: loops run
+// to DMAX_ and rows below DLO_ need no test (no branch in the unrolled loop).
 // ---------------------------------------------------------------------------
 __host__ __device__ constexpr int ceil_log2(int v) { return v <= 1 ? 0 : 1 + ceil_log2((v + 1) / 2); }
 __host__ __device__ constexpr int round_up(int v, int m) { return (v + m - 1) / m * m; }
@@ -271,15 +273,17 @@ __host__ __device__ constexpr BlkLayout make_layout_c(int d, int n)
     return BlkLayout{h, es, dn, ts, r, ls, h + d * r};
 }
 
-template <typename T, int D_, int NB_>
+template <typename T, int D_, int NB_, int DMAX_ = DMAX, int DLO_ = 1>
 struct Shape {
     static constexpr bool kD = D_ > 0, kN = NB_ > 0;
-    static constexpr int DM = kD ? D_ : DMAX;  // unrolled loop bound
+    static constexpr int DM = kD ? D_ : DMAX_;  // unrolled loop bound
+    static constexpr int DLO = kD ? D_ : DLO_;  // rows below this always exist
     static constexpr BlkLayout C = make_layout_c<T>(kD ? D_ : 1, kN ? NB_ : 1);
     const BlkLayout L;
     const int d_rt, n_rt;
     __device__ __forceinline__ Shape(const BlkLayout& l, int d, int n) : L(l), d_rt(d), n_rt(n) {}
     __device__ __forceinline__ int d() const { return kD ? D_ : d_rt; }
+    __device__ __forceinline__ bool has(int k) const { return k < DLO || k < d(); }
     __device__ __forceinline__ int n() const { return kN ? NB_ : n_rt; }
     __device__ __forceinline__ int H() const { return kN ? C.H : L.H; }
     __device__ __forceinline__ int R() const { return kN ? C.R : L.R; }
@@ -339,7 +343,7 @@ __device__ __forceinline__ void forward_call(const Params& P, const SH& sh, int 
     T g = T(1);
 #pragma unroll
     for (int k = 0; k < SH::DM; ++k) {
-        if (k < d) {
+        if (sh.has(k)) {
             const uint64_t t = (2ull * X[k] + 1ull) * (uint64_t)n;
             const int j = (int)(t >> 33);
             const T fr = Prec<T>::frac(t & ((1ull << 33) - 1ull));
@@ -361,7 +365,7 @@ __device__ __forceinline__ void forward_call(const Params& P, const SH& sh, int 
 #pragma unroll
     for (int k = 0; k < SH::DM; ++k) {
         p[k] = x[k];
-        if (k < d) {
+        if (sh.has(k)) {
             if ((mask >> k) & 1u) {
                 const int s = (int)((slotpack >> (4 * k)) & 0xFu);
                 const int kind = (kinds >> (8 * s)) & 0xff;
@@ -412,7 +416,7 @@ __device__ __forceinline__ void channel_rows(const Params& P, const SH& sh, cons
     const T gc = Prec<T>::gcen(P), k2 = Prec<T>::gk2(P);
 #pragma unroll
     for (int k = 0; k < SH::DM; ++k) {
-        if (k < d) {
+        if (sh.has(k)) {
             T xk[CPT];
 #pragma unroll
             for (int q = 0; q < CPT; ++q) xk[q] = p[q][k];

@@ -144,7 +144,7 @@ __device__ __forceinline__ void phase_c_int(const SH& sh, const Calls<T, CPT, SH
         const double w2 = w * w;
 #pragma unroll
         for (int k = 0; k < DM; ++k)
-            if (k < d) atomicAdd(&Ds[k * n + ((C.jp[q][k >> 2] >> (8 * (k & 3))) & 0xff)], w2);
+            if (sh.has(k)) atomicAdd(&Ds[k * n + ((C.jp[q][k >> 2] >> (8 * (k & 3))) & 0xff)], w2);
     }
 }
 
@@ -338,7 +338,7 @@ __global__ void __launch_bounds__(PASS_THREADS, MINB) k_pass(Params P, PassArgs 
                     float* pf = reinterpret_cast<float*>(rec);
 #pragma unroll
                     for (int k = 0; k < DM; ++k)
-                        if (k < d) pf[k] = (float)C.p[q][k];
+                        if (sh.has(k)) pf[k] = (float)C.p[q][k];
                     if (d & 1) pf[d] = 0.0f;
                     *reinterpret_cast<double*>(rec + A.rec_bytes - 8) = w;
                     A.callidx[slot] = (uint32_t)(base + (int64_t)q * PASS_THREADS + tid);

@@ -13,6 +13,11 @@
 // request that arrives while others are on the GPU joins the next tick.
 // Grids, α and running maxima stay resident on the device for the whole life
 // of a request.  Latency = arrival to completion.
+//
+// Nothing on the request path synchronises the device: request memory comes
+// from the server's own stream-ordered pool (cudaMallocFromPoolAsync /
+// cudaFreeAsync on the request's stream), and the request's stream, event
+// and pinned status slot are taken from a pool of lanes and given back.
 #include "../../include/vamp.h"
 #include "vamp_device.cuh"
 #include "vamp_internal.h"
@@ -64,6 +69,7 @@ struct Req {
     int tile = 1, grid_gen = 0;
     size_t smem_int = 0, smem_gen = 0;
     int64_t chunk = 0, nchunks = 0, gen_batch = 0;
+    int lane = -1;             // index into the server's lanes
     cudaStream_t stream = nullptr;
     cudaEvent_t ev = nullptr;
     Scalars* h_head = nullptr;
@@ -95,6 +101,19 @@ struct vamp_server {
     bool stop = false;
     uint64_t next_id = 1;
     std::string err;
+    // reusable per-request resources
+    cudaMemPool_t pool = nullptr;
+    struct Lane {
+        cudaStream_t stream = nullptr;
+        cudaEvent_t ev = nullptr;
+    };
+    std::vector<Lane> lanes;
+    std::vector<int> free_lanes;
+    unsigned char* h_heads = nullptr;  // pinned, one status slot per lane
+    size_t head_stride = 0;
+    // launch shape of the multi-instance kernel (cached per shared-memory size)
+    size_t tick_smem = 0;
+    int tick_grid = 0;
     // multi-instance launch arrays (capacity grows on demand)
     void* marena = nullptr;
     size_t mcap_inst = 0, mcap_pairs = 0;
@@ -126,13 +145,25 @@ struct vamp_server {
 
 namespace {
 
+// Takes a lane (stream, event, status slot), creating its stream and event
+// on first use.  -1 if they cannot be created.
+int take_lane(vamp_server* s)
+{
+    if (s->free_lanes.empty()) return -1;
+    const int i = s->free_lanes.back();
+    vamp_server::Lane& l = s->lanes[i];
+    if (!l.stream && cudaStreamCreateWithFlags(&l.stream, cudaStreamNonBlocking) != cudaSuccess) return -1;
+    if (!l.ev && cudaEventCreateWithFlags(&l.ev, cudaEventDisableTiming) != cudaSuccess) return -1;
+    s->free_lanes.pop_back();
+    return i;
+}
+
+// Returns a request's memory to the pool (ordered after its work on its
+// stream) and its lane to the free list; no device synchronisation.
 void free_req(vamp_server* s, Req* r)
 {
-    if (r->stream) cudaStreamSynchronize(r->stream);
-    cudaFree(r->mem);
-    if (r->ev) cudaEventDestroy(r->ev);
-    if (r->stream) cudaStreamDestroy(r->stream);
-    cudaFreeHost(r->h_head);
+    if (r->mem) cudaFreeAsync(r->mem, r->stream);
+    if (r->lane >= 0) s->free_lanes.push_back(r->lane);
     s->used_mem -= (int64_t)r->bytes;
     delete r;
 }
@@ -162,8 +193,13 @@ size_t request_bytes(const Req* r, size_t* o_stage, size_t* o_call, size_t* o_cn
 vamp_status admit(vamp_server* s, Req* r)
 {
     size_t o_stage, o_call, o_cnt, o_off;
+    r->lane = take_lane(s);
+    if (r->lane < 0) return VAMP_ERR_CUDA;
+    r->stream = s->lanes[r->lane].stream;
+    r->ev = s->lanes[r->lane].ev;
+    r->h_head = reinterpret_cast<Scalars*>(s->h_heads + (size_t)r->lane * s->head_stride);
     r->bytes = request_bytes(r, &o_stage, &o_call, &o_cnt, &o_off);
-    cudaError_t e = cudaMalloc(&r->mem, r->bytes);
+    cudaError_t e = cudaMallocFromPoolAsync(&r->mem, r->bytes, s->pool, r->stream);
     if (e != cudaSuccess) { r->mem = nullptr; r->bytes = 0; return VAMP_ERR_OOM; }
     s->used_mem += (int64_t)r->bytes;
     unsigned char* base = (unsigned char*)r->mem;
@@ -172,9 +208,6 @@ vamp_status admit(vamp_server* s, Req* r)
     r->callidx = (uint32_t*)(base + o_call);
     r->counts = (int*)(base + o_cnt);
     r->offsets = (long long*)(base + o_off);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&r->stream, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaMallocHost((void**)&r->h_head, sizeof(Scalars));
     const Params& P = r->P;
     const size_t rows = (size_t)P.K * P.d;
     std::vector<double> edges(rows * (P.n + 1)), alpha(P.K, 1.0 / (double)P.K);
@@ -267,11 +300,15 @@ vamp_status tick_integrate(vamp_server* s, std::vector<Req*>& ints)
     }
     s->h_it->iteration = 0;
     s->h_it->adapt = 3;
-    const void* fn = vamp::pass_multi_kernel(s->fp32);
-    int bps = 0;
-    if (vamp::ensure_smem(fn, smem) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, vamp::PASS_THREADS, smem) != cudaSuccess)
-        return VAMP_ERR_CUDA;
+    if (smem != s->tick_smem) {
+        const void* fn = vamp::pass_multi_kernel(s->fp32);
+        int bps = 0;
+        if (vamp::ensure_smem(fn, smem) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, vamp::PASS_THREADS, smem) != cudaSuccess)
+            return VAMP_ERR_CUDA;
+        s->tick_smem = smem;
+        s->tick_grid = (bps > 0 ? bps : 1) * s->sm_count;
+    }
     cudaStream_t st0 = s->stream;
     cudaError_t e = cudaMemcpyAsync(s->d_inst, s->h_inst, n * sizeof(Params), cudaMemcpyHostToDevice, st0);
     if (e == cudaSuccess) e = cudaMemcpyAsync(s->d_tiles, s->h_tiles, n * 4, cudaMemcpyHostToDevice, st0);
@@ -297,9 +334,9 @@ vamp_status tick_integrate(vamp_server* s, std::vector<Req*>& ints)
     M.npairs = (int)npairs;
     M.nrows = s->h_row_off[n];
     M.max_n = max_n;
-    M.item_calls = (int64_t)vamp::PASS_THREADS * 4;
+    M.item_calls = (int64_t)vamp::PASS_THREADS * 16;
     if (e == cudaSuccess) e = vamp::launch_batch_begin(M, st0);
-    if (e == cudaSuccess) e = vamp::launch_pass_multi(s->fp32, M, (bps > 0 ? bps : 1) * s->sm_count, smem, st0);
+    if (e == cudaSuccess) e = vamp::launch_pass_multi(s->fp32, M, s->tick_grid, smem, st0);
     if (e == cudaSuccess) e = vamp::launch_batch_after(M, st0);
     if (e == cudaSuccess) e = cudaMemcpyAsync(s->h_results, s->d_results, (size_t)n * 9 * 8, cudaMemcpyDeviceToHost, st0);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st0);
@@ -478,6 +515,22 @@ vamp_status vamp_server_create(int32_t max_slots, int64_t mem_budget_bytes, int3
         delete s;
         return VAMP_ERR_CUDA;
     }
+    // the server's own memory pool: freed request memory stays in it (up to
+    // the budget) for the next requests
+    cudaMemPoolProps pp{};
+    pp.allocType = cudaMemAllocationTypePinned;
+    pp.location.type = cudaMemLocationTypeDevice;
+    pp.location.id = s->dev;
+    s->head_stride = (offsetof(Scalars, n_hist) + 127) & ~size_t(127);
+    s->lanes.resize(max_slots);
+    for (int i = max_slots - 1; i >= 0; --i) s->free_lanes.push_back(i);
+    if (cudaMemPoolCreate(&s->pool, &pp) != cudaSuccess ||
+        cudaMallocHost((void**)&s->h_heads, s->head_stride * (size_t)max_slots) != cudaSuccess) {
+        vamp_server_destroy(s);
+        return VAMP_ERR_CUDA;
+    }
+    uint64_t keep = (uint64_t)mem_budget_bytes;
+    cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &keep);
     s->th = std::thread(scheduler, s);
     *out = s;
     return VAMP_OK;
@@ -588,6 +641,13 @@ void vamp_server_destroy(vamp_server* s)
     s->cv.notify_one();
     if (s->th.joinable()) s->th.join();
     for (Req* r : s->active) free_req(s, r);
+    cudaDeviceSynchronize();  // frees and work of the lanes' streams
+    for (vamp_server::Lane& l : s->lanes) {
+        if (l.ev) cudaEventDestroy(l.ev);
+        if (l.stream) cudaStreamDestroy(l.stream);
+    }
+    if (s->pool) cudaMemPoolDestroy(s->pool);
+    cudaFreeHost(s->h_heads);
     cudaFree(s->marena);
     cudaFreeHost(s->hmem);
     if (s->stream) cudaStreamDestroy(s->stream);
