@@ -278,6 +278,7 @@ struct Shape {
     static constexpr bool kD = D_ > 0, kN = NB_ > 0;
     static constexpr int DM = kD ? D_ : DMAX_;  // unrolled loop bound
     static constexpr int DLO = kD ? D_ : DLO_;  // rows below this always exist
+    static constexpr int NBC = NB_;              // compile-time bins (0: runtime)
     static constexpr BlkLayout C = make_layout_c<T>(kD ? D_ : 1, kN ? NB_ : 1);
     const BlkLayout L;
     const int d_rt, n_rt;

@@ -124,14 +124,30 @@ __device__ __forceinline__ void tile_compute(const Params& P, const SH& sh, cons
     }
 }
 
+// Word i of a small register array, by a chain of selects (no local memory).
+template <int W>
+__device__ __forceinline__ uint32_t pick(const uint32_t (&a)[W], int i)
+{
+    uint32_t v = a[0];
+#pragma unroll
+    for (int t = 1; t < W; ++t) v = i == t ? a[t] : v;
+    return v;
+}
+
 // Phase C of an integration batch: shifted sums, max weight and the d-values
-// of the segment's channel in shared memory.
+// (Eq. 15) of the segment's channel in shared memory (FP64 atomics, which
+// retry on collisions).  Unless the shape has many bins per axis (a lane's
+// bins then rarely collide), lane l adds its d terms in the rotated axis
+// order l, l+1, ... (mod d), so that at any step the lanes of a warp hit
+// different rows.
 template <typename T, int CPT, class SH>
 __device__ __forceinline__ void phase_c_int(const SH& sh, const Calls<T, CPT, SH::DM>& C, double sft, double* Ds,
                                             double& s1, double& s2, double& wm, bool& bad)
 {
     constexpr int DM = SH::DM;
     const int d = sh.d(), n = sh.n();
+    constexpr bool kRotate = !(SH::kN && SH::NBC >= 64);
+    const int rot = kRotate ? (threadIdx.x & 31) % d : 0;
 #pragma unroll
     for (int q = 0; q < CPT; ++q) {
         if (!C.valid[q]) continue;
@@ -143,8 +159,18 @@ __device__ __forceinline__ void phase_c_int(const SH& sh, const Calls<T, CPT, SH
         wm = fmax(wm, w);
         const double w2 = w * w;
 #pragma unroll
-        for (int k = 0; k < DM; ++k)
-            if (sh.has(k)) atomicAdd(&Ds[k * n + ((C.jp[q][k >> 2] >> (8 * (k & 3))) & 0xff)], w2);
+        for (int s = 0; s < DM; ++s) {
+            if (sh.has(s)) {
+                if (kRotate) {
+                    int k = s + rot;
+                    if (k >= d) k -= d;
+                    const int j = (pick(C.jp[q], k >> 2) >> (8 * (k & 3))) & 0xff;
+                    atomicAdd(&Ds[k * n + j], w2);
+                } else {
+                    atomicAdd(&Ds[s * n + ((C.jp[q][s >> 2] >> (8 * (s & 3))) & 0xff)], w2);
+                }
+            }
+        }
     }
 }
 
