@@ -74,7 +74,8 @@ struct Req {
     cudaEvent_t ev = nullptr;
     Scalars* h_head = nullptr;
     // progress
-    int phase = 0;  // 1 integrating, 2 generating, 3 done
+    int phase = 0;  // 0 setting up, 1 integrating, 2 generating, 3 done
+    bool in_tick = false;  // member of the multi-instance launch in flight
     int it_done = 0;
     int64_t calls_total = 0;
     vamp_pass_result last{};
@@ -114,6 +115,8 @@ struct vamp_server {
     // launch shape of the multi-instance kernel (cached per shared-memory size)
     size_t tick_smem = 0;
     int tick_grid = 0;
+    cudaEvent_t tick_ev = nullptr;     // end of the launch in flight
+    std::vector<Req*> tick_reqs;       // its members
     // multi-instance launch arrays (capacity grows on demand)
     void* marena = nullptr;
     size_t mcap_inst = 0, mcap_pairs = 0;
@@ -189,7 +192,9 @@ size_t request_bytes(const Req* r, size_t* o_stage, size_t* o_call, size_t* o_cn
     return off;
 }
 
-// Allocates and initialises an admitted request (scheduler thread).
+// Allocates an admitted request and enqueues its initialisation on its
+// stream (uniform grids, α = 1/K, lookup blocks); the request joins the
+// integration launches once the recorded event has completed.
 vamp_status admit(vamp_server* s, Req* r)
 {
     size_t o_stage, o_call, o_cnt, o_off;
@@ -218,7 +223,7 @@ vamp_status admit(vamp_server* s, Req* r)
     if (e == cudaSuccess) e = cudaMemcpyAsync(P.alpha, alpha.data(), P.K * 8, cudaMemcpyHostToDevice, r->stream);
     if (e == cudaSuccess) e = vamp::upload_setup(P, r->S, r->stream);
     if (e == cudaSuccess) e = vamp::launch_derive(P, r->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(r->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(r->ev, r->stream);  // setup done (polled)
     if (e != cudaSuccess) return VAMP_ERR_CUDA;
     // generation kernel of this shape
     vamp::pass_smem_for(P, s->fp32, r->var->minb, &r->tile, &r->smem_int, &r->smem_gen);
@@ -232,7 +237,8 @@ vamp_status admit(vamp_server* s, Req* r)
     r->nchunks = (r->gen_batch + r->chunk - 1) / r->chunk;
     r->grid_gen = (int)std::min<int64_t>(r->nchunks, (int64_t)(bps > 0 ? bps : 1) * s->sm_count);
     r->t_admit = clk::now();
-    r->phase = 1;
+    r->phase = 0;
+    r->in_flight = true;
     return VAMP_OK;
 }
 
@@ -268,8 +274,10 @@ vamp_status grow_multi(vamp_server* s, size_t n, size_t npairs)
     return VAMP_OK;
 }
 
-// One iteration of every integrating request in one multi-instance launch.
-vamp_status tick_integrate(vamp_server* s, std::vector<Req*>& ints)
+// Enqueues one iteration of every request in ints as one multi-instance
+// launch on the server stream; tick_finish reads the results once the
+// recorded event has completed.
+vamp_status tick_launch(vamp_server* s, const std::vector<Req*>& ints)
 {
     const int n = (int)ints.size();
     size_t npairs = 0;
@@ -339,10 +347,19 @@ vamp_status tick_integrate(vamp_server* s, std::vector<Req*>& ints)
     if (e == cudaSuccess) e = vamp::launch_pass_multi(s->fp32, M, s->tick_grid, smem, st0);
     if (e == cudaSuccess) e = vamp::launch_batch_after(M, st0);
     if (e == cudaSuccess) e = cudaMemcpyAsync(s->h_results, s->d_results, (size_t)n * 9 * 8, cudaMemcpyDeviceToHost, st0);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st0);
+    if (e == cudaSuccess) e = cudaEventRecord(s->tick_ev, st0);
     if (e != cudaSuccess) return VAMP_ERR_CUDA;
+    for (Req* r : ints) r->in_tick = true;
+    return VAMP_OK;
+}
+
+// Results of the launch in flight (its event has completed).
+void tick_finish(vamp_server* s, const std::vector<Req*>& ints)
+{
+    const int n = (int)ints.size();
     for (int i = 0; i < n; ++i) {
         Req* r = ints[i];
+        r->in_tick = false;
         const double* x = s->h_results + (size_t)i * 9;
         r->last.integral = x[0];
         r->last.variance = x[1];
@@ -358,7 +375,6 @@ vamp_status tick_integrate(vamp_server* s, std::vector<Req*>& ints)
         if (++r->it_done >= r->iterations) r->phase = r->n_events > 0 ? 2 : 3;
     }
     ++s->n_ticks;
-    return VAMP_OK;
 }
 
 // Starts the next generation batch of a request on its own stream.
@@ -416,8 +432,10 @@ void complete(vamp_server* s, Req* r)
 void scheduler(vamp_server* s)
 {
     cudaSetDevice(s->dev);
+    bool tick_running = false;
     for (;;) {
-        // ---- admission ---------------------------------------------------
+        bool progress = false;
+        // ---- admission (initialisation enqueued on the request's stream) --
         std::vector<Req*> admitted;
         {
             std::unique_lock<std::mutex> lk(s->mu);
@@ -439,6 +457,7 @@ void scheduler(vamp_server* s)
             }
         }
         for (Req* r : admitted) {
+            progress = true;
             r->status = admit(s, r);
             if (r->status != VAMP_OK) {
                 r->t_admit = clk::now();
@@ -448,25 +467,29 @@ void scheduler(vamp_server* s)
             }
             s->active.push_back(r);
         }
-        // ---- generation batches on per-request streams (overlap) ----------
-        for (Req* r : s->active)
-            if (r->phase == 2 && !r->in_flight && r->status == VAMP_OK) r->status = gen_launch(s, r);
-        // ---- one iteration of every integrating request ------------------
-        std::vector<Req*> ints;
-        for (Req* r : s->active)
-            if (r->phase == 1 && r->status == VAMP_OK) ints.push_back(r);
-        if (!ints.empty()) {
-            const vamp_status st = tick_integrate(s, ints);
-            if (st != VAMP_OK)
-                for (Req* r : ints) r->status = st;
-        } else {
-            std::this_thread::sleep_for(std::chrono::microseconds(50));
+        // ---- the integration launch in flight ---------------------------
+        if (tick_running) {
+            const cudaError_t q = cudaEventQuery(s->tick_ev);
+            if (q == cudaSuccess) {
+                tick_finish(s, s->tick_reqs);
+                tick_running = false;
+                progress = true;
+            } else if (q != cudaErrorNotReady) {
+                for (Req* r : s->tick_reqs) { r->in_tick = false; r->status = VAMP_ERR_CUDA; }
+                tick_running = false;
+            }
         }
-        // ---- finished generation batches, completed requests -------------
-        std::vector<Req*> keep;
+        // ---- per request: setup done, generation batches ----------------
         for (Req* r : s->active) {
-            if (r->phase == 2 && r->in_flight && cudaEventQuery(r->ev) == cudaSuccess) {
-                r->in_flight = false;
+            if (r->status != VAMP_OK || !r->in_flight) continue;
+            const cudaError_t q = cudaEventQuery(r->ev);
+            if (q == cudaErrorNotReady) continue;
+            r->in_flight = false;
+            progress = true;
+            if (q != cudaSuccess) { r->status = VAMP_ERR_CUDA; continue; }
+            if (r->phase == 0) {
+                r->phase = 1;
+            } else if (r->phase == 2) {
                 r->written += r->h_head->gen_take;
                 r->used += r->h_head->gen_used;
                 r->over += r->h_head->gen_over;
@@ -474,23 +497,53 @@ void scheduler(vamp_server* s)
                 ++r->gen_b;
                 if (r->written >= r->n_events) r->phase = 3;
             }
-            if (r->status != VAMP_OK && !r->in_flight) r->phase = 3;
+        }
+        // ---- next integration launch: every ready integrating request ----
+        if (!tick_running) {
+            s->tick_reqs.clear();
+            for (Req* r : s->active)
+                if (r->phase == 1 && r->status == VAMP_OK && !r->in_flight) s->tick_reqs.push_back(r);
+            if (!s->tick_reqs.empty()) {
+                const vamp_status st = tick_launch(s, s->tick_reqs);
+                if (st != VAMP_OK)
+                    for (Req* r : s->tick_reqs) r->status = st;
+                else
+                    tick_running = true;
+                progress = true;
+            }
+        }
+        // ---- generation batches on the requests' streams (overlap) -------
+        for (Req* r : s->active)
+            if (r->phase == 2 && !r->in_flight && r->status == VAMP_OK) {
+                r->status = gen_launch(s, r);
+                progress = true;
+            }
+        // ---- completed requests ------------------------------------------
+        std::vector<Req*> keep;
+        for (Req* r : s->active) {
+            if (r->in_tick || r->in_flight) {
+                keep.push_back(r);
+                continue;
+            }
+            if (r->status != VAMP_OK) r->phase = 3;
             if (r->phase == 3) {
                 complete(s, r);
                 free_req(s, r);
+                progress = true;
             } else {
                 keep.push_back(r);
             }
         }
         s->active.swap(keep);
         int32_t ni = 0, ng = 0;
-        for (Req* r : s->active) (r->phase == 1 ? ni : ng) += 1;
+        for (Req* r : s->active) (r->phase <= 1 ? ni : ng) += 1;
         s->n_integrating = ni;
         s->n_generating = ng;
         {
             std::lock_guard<std::mutex> lk(s->mu);
             s->n_queued = (int32_t)s->queue.size();
         }
+        if (!progress) std::this_thread::sleep_for(std::chrono::microseconds(20));
     }
 }
 
@@ -525,6 +578,7 @@ vamp_status vamp_server_create(int32_t max_slots, int64_t mem_budget_bytes, int3
     s->lanes.resize(max_slots);
     for (int i = max_slots - 1; i >= 0; --i) s->free_lanes.push_back(i);
     if (cudaMemPoolCreate(&s->pool, &pp) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s->tick_ev, cudaEventDisableTiming) != cudaSuccess ||
         cudaMallocHost((void**)&s->h_heads, s->head_stride * (size_t)max_slots) != cudaSuccess) {
         vamp_server_destroy(s);
         return VAMP_ERR_CUDA;
@@ -640,6 +694,7 @@ void vamp_server_destroy(vamp_server* s)
     }
     s->cv.notify_one();
     if (s->th.joinable()) s->th.join();
+    if (s->stream) cudaStreamSynchronize(s->stream);  // a launch still in flight
     for (Req* r : s->active) free_req(s, r);
     cudaDeviceSynchronize();  // frees and work of the lanes' streams
     for (vamp_server::Lane& l : s->lanes) {
@@ -647,6 +702,7 @@ void vamp_server_destroy(vamp_server* s)
         if (l.stream) cudaStreamDestroy(l.stream);
     }
     if (s->pool) cudaMemPoolDestroy(s->pool);
+    if (s->tick_ev) cudaEventDestroy(s->tick_ev);
     cudaFreeHost(s->h_heads);
     cudaFree(s->marena);
     cudaFreeHost(s->hmem);
