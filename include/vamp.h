@@ -235,8 +235,10 @@ typedef struct vamp_batch vamp_batch;
 
 /* Creates the batch on the current device with its own CUDA stream; cfgs[i]
  * as for vamp_create (all with the same precision).  autotune_tiles = 1: the
- * first iteration times work-item sizes and shared-memory budgets once and
- * keeps the fastest; 0: one batch of calls per item, 112 KB per CTA. */
+ * first iteration times work-item sizes (512, 2048, 8192 calls) and
+ * shared-memory budgets (112 KB per CTA with two CTAs per SM, or, in the
+ * FP32-eval form, 72 KB with three) once and keeps the fastest; 0: 512 calls
+ * per item, 112 KB per CTA. */
 vamp_status vamp_batch_create(const vamp_config *cfgs, int32_t n, int32_t autotune_tiles, vamp_batch **out);
 
 /* One adaptation iteration of every instance: n_calls[i] calls (host array),
@@ -251,7 +253,7 @@ vamp_status vamp_batch_get_state(vamp_batch *b, int32_t instance, double *edges,
                                  double *w_max);
 
 /* The launch shape in use and the autotuner's timings of one pass (tuned and
- * fixed shape, at an eighth of the first iteration's calls; 0 if untuned). */
+ * fixed shape, at the first iteration's calls; 0 if untuned). */
 vamp_status vamp_batch_tuning(const vamp_batch *b, int64_t *item_calls, int32_t *budget_kb, double *tuned_ms,
                               double *fixed_ms);
 

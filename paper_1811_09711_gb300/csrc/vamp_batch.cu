@@ -47,6 +47,7 @@ struct vamp_batch {
     // launch shape
     int64_t item_calls = 0;
     int budget_kb = 112;
+    int minb = 2;                   // CTAs per SM of the multi-instance kernel in use
     size_t smem = 0;
     int grid = 0;
     int tune = 1, tuned = 0;
@@ -103,6 +104,7 @@ vamp::MultiArgs margs(const vamp_batch* b)
 vamp_status apply_shape(vamp_batch* b, int budget_kb, int64_t item_calls)
 {
     const size_t budget = (size_t)budget_kb * 1024;
+    b->minb = budget_kb > 80 ? 2 : 3;  // 112 KB: two CTAs per SM; 72 KB: three
     size_t smem = 0;
     for (int i = 0; i < b->n; ++i) {
         const size_t ds = (size_t)b->d[i] * b->nb[i] * 8;
@@ -116,9 +118,9 @@ vamp_status apply_shape(vamp_batch* b, int budget_kb, int64_t item_calls)
     int maxsm = 0;
     BCK(b, cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->dev));
     if ((int)smem > maxsm) return bfail(b, VAMP_ERR_INVALID_ARG, "an instance's grid is too large for shared memory");
-    BCK(b, vamp::ensure_smem(vamp::pass_multi_kernel(b->fp32), smem));
+    BCK(b, vamp::ensure_smem(vamp::pass_multi_kernel(b->fp32, b->minb), smem));
     int bps = 0;
-    BCK(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, vamp::pass_multi_kernel(b->fp32), vamp::PASS_THREADS,
+    BCK(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, vamp::pass_multi_kernel(b->fp32, b->minb), vamp::PASS_THREADS,
                                                          smem));
     BCK(b, cudaMemcpyAsync(b->d_tiles, b->tiles.data(), b->n * sizeof(int), cudaMemcpyHostToDevice, b->stream));
     b->smem = smem;
@@ -144,7 +146,7 @@ vamp_status enqueue_iteration(vamp_batch* b, bool pass_only)
     BCK(b, cudaMemcpyAsync(b->d_iter, b->h_iter, b->n * sizeof(uint32_t), cudaMemcpyHostToDevice, b->stream));
     const vamp::MultiArgs M = margs(b);
     BCK(b, vamp::launch_batch_begin(M, b->stream));
-    BCK(b, vamp::launch_pass_multi(b->fp32, M, b->grid, b->smem, b->stream));
+    BCK(b, vamp::launch_pass_multi(b->fp32, b->minb, M, b->grid, b->smem, b->stream));
     if (pass_only) return VAMP_OK;
     BCK(b, vamp::launch_batch_after(M, b->stream));
     BCK(b, cudaMemcpyAsync(b->h_results, b->d_results, (size_t)b->n * 9 * sizeof(double), cudaMemcpyDeviceToHost,
@@ -152,20 +154,21 @@ vamp_status enqueue_iteration(vamp_batch* b, bool pass_only)
     return VAMP_OK;
 }
 
-// Autotuner: times the pass of one iteration (at an eighth of the requested
-// calls) for work-item sizes x shared-memory budgets and keeps the fastest;
-// the fixed shape (one batch per item, 112 KB) is timed too, for reference.
+// Autotuner: times the pass of one iteration at the requested calls (once
+// per shape after a warm-up launch) for work-item sizes x shared-memory
+// budgets and keeps the fastest; the fixed shape (one batch per item,
+// 112 KB) is timed too, for reference.
 vamp_status autotune(vamp_batch* b, const int64_t* n_calls)
 {
     const int64_t B = (int64_t)vamp::PASS_THREADS * calls_per_thread(b->fp32);
-    for (int i = 0; i < b->n; ++i) b->h_ncalls[i] = std::max<int64_t>(1, n_calls[i] / 8);
+    for (int i = 0; i < b->n; ++i) b->h_ncalls[i] = n_calls[i];
     b->h_it->iteration = 0x7fffffffu;
     b->h_it->adapt = 0;
     for (int i = 0; i < b->n; ++i) b->h_iter[i] = 0x7fffffffu;
     cudaEvent_t e0, e1;
     BCK(b, cudaEventCreate(&e0));
     BCK(b, cudaEventCreate(&e1));
-    const int budgets[2] = {112, 64};
+    const int budgets[2] = {112, 72};
     const int64_t mults[3] = {1, 4, 16};
     float best = 1e30f;
     int best_budget = 112;

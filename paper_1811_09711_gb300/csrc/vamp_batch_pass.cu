@@ -108,8 +108,8 @@ __device__ __forceinline__ bool run_item(const MultiArgs& M, const Params& P, Sm
     return true;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(PASS_THREADS, 2) k_pass_multi(MultiArgs M)
+template <typename T, int MINB>
+__global__ void __launch_bounds__(PASS_THREADS, MINB) k_pass_multi(MultiArgs M)
 {
     static_assert(sizeof(Params) <= PARAMS_SLOT, "Params does not fit its shared-memory slot");
     extern __shared__ __align__(128) unsigned char smem[];
@@ -171,15 +171,18 @@ __global__ void __launch_bounds__(PASS_THREADS, 2) k_pass_multi(MultiArgs M)
     }
 }
 
-const void* pass_multi_kernel(int fp32)
+// Compiled for two or (FP32-eval) three CTAs per SM.
+const void* pass_multi_kernel(int fp32, int minb)
 {
-    return fp32 ? (const void*)k_pass_multi<float> : (const void*)k_pass_multi<double>;
+    if (!fp32) return (const void*)k_pass_multi<double, 2>;
+    return minb >= 3 ? (const void*)k_pass_multi<float, 3> : (const void*)k_pass_multi<float, 2>;
 }
 
-cudaError_t launch_pass_multi(int fp32, const MultiArgs& M, int grid, size_t smem, cudaStream_t s)
+cudaError_t launch_pass_multi(int fp32, int minb, const MultiArgs& M, int grid, size_t smem, cudaStream_t s)
 {
-    if (fp32) k_pass_multi<float><<<grid, PASS_THREADS, smem, s>>>(M);
-    else k_pass_multi<double><<<grid, PASS_THREADS, smem, s>>>(M);
+    if (!fp32) k_pass_multi<double, 2><<<grid, PASS_THREADS, smem, s>>>(M);
+    else if (minb >= 3) k_pass_multi<float, 3><<<grid, PASS_THREADS, smem, s>>>(M);
+    else k_pass_multi<float, 2><<<grid, PASS_THREADS, smem, s>>>(M);
     return cudaGetLastError();
 }
 

@@ -128,8 +128,9 @@ constexpr int PARAMS_SLOT = 512;  // bytes reserved for an instance's Params in 
 
 cudaError_t launch_batch_begin(const MultiArgs& M, cudaStream_t s);
 cudaError_t launch_batch_after(const MultiArgs& M, cudaStream_t s);  // finish, refine, α, gather
-cudaError_t launch_pass_multi(int fp32, const MultiArgs& M, int grid, size_t smem, cudaStream_t s);
-const void* pass_multi_kernel(int fp32);
+// minb: CTAs per SM the kernel is compiled for (2, or 3 in the FP32-eval form)
+cudaError_t launch_pass_multi(int fp32, int minb, const MultiArgs& M, int grid, size_t smem, cudaStream_t s);
+const void* pass_multi_kernel(int fp32, int minb);
 
 cudaError_t launch_begin_pass(const Params& P, int64_t N, cudaStream_t s);
 cudaError_t launch_finish_pass(const Params& P, int combine, cudaStream_t s);

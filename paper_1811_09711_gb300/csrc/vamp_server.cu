@@ -112,7 +112,11 @@ struct vamp_server {
     std::vector<int> free_lanes;
     unsigned char* h_heads = nullptr;  // pinned, one status slot per lane
     size_t head_stride = 0;
-    // launch shape of the multi-instance kernel (cached per shared-memory size)
+    // launch shape of the multi-instance kernel: three CTAs per SM with 72 KB
+    // each in the FP32-eval form (the batch autotuner's usual pick for mixed
+    // request shapes), two with 112 KB in FP64; cached per shared-memory size
+    int tick_minb = 2;
+    size_t tick_budget = vamp::TILE_BUDGET;
     size_t tick_smem = 0;
     int tick_grid = 0;
     cudaEvent_t tick_ev = nullptr;     // end of the launch in flight
@@ -294,7 +298,7 @@ vamp_status tick_launch(vamp_server* s, const std::vector<Req*>& ints)
         const size_t S = (size_t)(s->fp32 ? P.lay32.bytes : P.lay64.bytes);
         const size_t ds = (size_t)P.d * P.n * 8;
         const size_t fixed = vamp::SMEM_HEAD + vamp::PARAMS_SLOT + ds;
-        long t = vamp::TILE_BUDGET > fixed ? (long)((vamp::TILE_BUDGET - fixed) / (2 * S)) : 1;
+        long t = s->tick_budget > fixed ? (long)((s->tick_budget - fixed) / (2 * S)) : 1;
         t = std::max(1L, std::min(t, (long)P.K));
         smem = std::max(smem, fixed + 2 * (size_t)t * S);
         s->h_inst[i] = P;
@@ -309,7 +313,7 @@ vamp_status tick_launch(vamp_server* s, const std::vector<Req*>& ints)
     s->h_it->iteration = 0;
     s->h_it->adapt = 3;
     if (smem != s->tick_smem) {
-        const void* fn = vamp::pass_multi_kernel(s->fp32);
+        const void* fn = vamp::pass_multi_kernel(s->fp32, s->tick_minb);
         int bps = 0;
         if (vamp::ensure_smem(fn, smem) != cudaSuccess ||
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, vamp::PASS_THREADS, smem) != cudaSuccess)
@@ -342,9 +346,9 @@ vamp_status tick_launch(vamp_server* s, const std::vector<Req*>& ints)
     M.npairs = (int)npairs;
     M.nrows = s->h_row_off[n];
     M.max_n = max_n;
-    M.item_calls = (int64_t)vamp::PASS_THREADS * 16;
+    M.item_calls = (int64_t)vamp::PASS_THREADS * 8;
     if (e == cudaSuccess) e = vamp::launch_batch_begin(M, st0);
-    if (e == cudaSuccess) e = vamp::launch_pass_multi(s->fp32, M, s->tick_grid, smem, st0);
+    if (e == cudaSuccess) e = vamp::launch_pass_multi(s->fp32, s->tick_minb, M, s->tick_grid, smem, st0);
     if (e == cudaSuccess) e = vamp::launch_batch_after(M, st0);
     if (e == cudaSuccess) e = cudaMemcpyAsync(s->h_results, s->d_results, (size_t)n * 9 * 8, cudaMemcpyDeviceToHost, st0);
     if (e == cudaSuccess) e = cudaEventRecord(s->tick_ev, st0);
@@ -562,6 +566,10 @@ vamp_status vamp_server_create(int32_t max_slots, int64_t mem_budget_bytes, int3
     s->max_slots = max_slots;
     s->budget = mem_budget_bytes;
     s->fp32 = precision == VAMP_PREC_FP32_EVAL;
+    if (s->fp32) {
+        s->tick_minb = 3;
+        s->tick_budget = 72 * 1024;
+    }
     if (cudaGetDevice(&s->dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&s->sm_count, cudaDevAttrMultiProcessorCount, s->dev) != cudaSuccess ||
         cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) {
