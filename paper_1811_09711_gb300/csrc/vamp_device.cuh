@@ -266,7 +266,9 @@ __host__ __device__ constexpr BlkLayout make_layout_c(int d, int n)
 {
     const int per16 = 16 / (int)sizeof(T);
     const int es = round_up(n + 1, per16), dn = round_up(n + 1, per16);
-    const int ls = ceil_log2(n) + 1 < 2 ? 2 : ceil_log2(n) + 1;
+    // about four cells per bin: on adapted grids nearly every row then has
+    // no cell overlapping more than two bins (the single-probe lookup)
+    const int ls = ceil_log2(n) + 2;
     const int ts = round_up((1 << ls) + 2, 16);
     const int h = (int)sizeof(ChanHdr<T>);
     const int r = (es + dn) * (int)sizeof(T) + ts;
