@@ -24,6 +24,11 @@ integrate-then-generate requests (200 req/s over a 60 s arrival window,
 continuous-batching server, wall-clock throughput and p50/p99 latency, for
 the FP32-eval form and (over a shorter window) the FP64 form.
 
+`fp32_accuracy`: the FP32-eval pass against the FP64 pass on the same grids,
+α and random stream -- integral deviation (relative and in σ), and on a
+sample of calls the inverse-lookup bin flips and per-call weight deviations.
+`cpu_baseline`: the FP64 oracle on all host cores and on one.
+
 --impl reference times the FP64 CPU oracle (the only reference this method
 has) on bounded samples of the same workload on the host cores.
 """
@@ -112,6 +117,28 @@ def _dist():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def replica_problem(base, rank: int):
+    """The workload of one rank: an independent replica of the problem on
+    its own random stream (request id = rank); no data crosses ranks."""
+    return base.replace(request_id=rank)
+
+
+def job_throughput(t_ms: float, calls: float, world_size: int, device="cpu"):
+    """Whole-job figures from per-rank ones: the slowest rank's time and
+    the calls of all ranks (one max- and one sum-reduction over the ranks'
+    process group; identity for one rank)."""
+    if world_size <= 1:
+        return t_ms, calls
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([t_ms, float(calls)], dtype=torch.float64, device=device)
+    mx = tt.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    sm = tt.clone()
+    dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+    return float(mx[0]), float(sm[1])
 
 
 KERNEL_SOURCES = ["vamp_pass.cuh", "vamp_device.cuh", "vamp_pass_f32_shapes.cu", "vamp_internal.h"]
@@ -289,7 +316,7 @@ def run_gpu(args):
     stream = torch.cuda.Stream(device=dev)
     base = P.collider()
     # independent replica per rank: its own random stream (request id)
-    pr = base.replace(request_id=rank)
+    pr = replica_problem(base, rank)
     N = pr.calls
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
@@ -337,15 +364,7 @@ def run_gpu(args):
     barrier()
     clk = clocks.stop()
     t_tot = sum(ms)
-    if ws > 1:
-        tt = torch.tensor([t_tot, float(calls)], dtype=torch.float64, device=dev)
-        mx = tt.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        sm = tt.clone()
-        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
-        t_max, calls_all = float(mx[0]), float(sm[1])
-    else:
-        t_max, calls_all = t_tot, float(calls)
+    t_max, calls_all = job_throughput(t_tot, float(calls), ws, dev)
     value = calls_all / (t_max / 1e3)
     g.profile(False)
 
@@ -403,8 +422,22 @@ def run_gpu(args):
     g64 = V.Vamp(pr, precision=V.PREC_FP64, stream=stream)
     st = g.get_state()
     g64.set_state(st["edges"], st["alpha"], st["shift"], st["w_max"])
-    g64.sample_pass(N, it)
+    r64 = g64.sample_pass(N, it)
     stream.synchronize()
+    # FP32-eval against FP64 on the same grids, α and random stream: the pass
+    # integral, and per call the inverse-lookup bins (flips) and weights
+    r32 = g.sample_pass(N, it)
+    ns = 4096
+    e32, e64 = g.eval_calls(0, it, 0, ns), g64.eval_calls(0, it, 0, ns)
+    ok = (e32["bins"] >= 0) & (e64["bins"] >= 0)
+    flips = int(np.sum(ok & (e32["bins"] != e64["bins"])))
+    wrel = np.abs(e32["w"] - e64["w"]) / np.maximum(np.abs(e64["w"]), 1e-300)
+    fp32_acc = {"integral_fp32": r32.integral, "integral_fp64": r64.integral,
+                "integral_rel_dev": abs(r32.integral - r64.integral) / abs(r64.integral),
+                "integral_dev_sigma": abs(r32.integral - r64.integral) / math.sqrt(max(r64.variance, 1e-300)),
+                "sample_calls": ns, "lookups": int(ok.sum()), "bin_flips": flips,
+                "bin_flips_per_lookup": flips / max(int(ok.sum()), 1),
+                "weight_rel_dev_median": float(np.median(wrel)), "weight_rel_dev_max": float(np.max(wrel))}
     f64_steps = max(1, min(args.steps, 3))
     ms64, calls64, _ = timed_steps(g64, f64_steps, it + 1, 0)
     fp64_rate = calls64 / (sum(ms64) / 1e3)
@@ -442,6 +475,7 @@ def run_gpu(args):
                       "parallelism": f"replicas{ws}", "l2": "flushed (256 MB write) between timed steps",
                       "precision": "FP32-eval"},
            "fp64_path": {"value": fp64_rate, "unit": UNIT, "speedup_fp32_eval": value / ws / fp64_rate},
+           "fp32_accuracy": fp32_acc,
            "generation": {"events": gst["n_written"], "events_per_s": gst["n_written"] / (gen_ms / 1e3),
                           "calls_used": gst["n_calls_used"], "overweight": gst["n_overweight"],
                           "gen_kernel_ms": gks["gen_ms"], "batches": gks["gen_launches"]},
@@ -456,8 +490,11 @@ def run_gpu(args):
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
         thr = os.cpu_count() or 1
         v, ncall, dt = cpu_oracle_rate(base, args.cpu_seconds, thr)
+        v1, ncall1, dt1 = cpu_oracle_rate(base, args.cpu_seconds / 4, 1)
         res["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": thr, "kind": "oracle",
-                               "sample": f"one oracle pass of {ncall} calls of the same workload ({dt:.1f} s)"}
+                               "sample": f"one oracle pass of {ncall} calls of the same workload ({dt:.1f} s)",
+                               "single_thread": {"value": v1, "unit": UNIT, "cores": 1,
+                                                 "sample": f"one oracle pass of {ncall1} calls ({dt1:.1f} s)"}}
     if rank == 0:
         print(json.dumps(res), flush=True)
     if ws > 1:

@@ -1,0 +1,62 @@
+"""The multi-GPU form of the benchmark: independent replicas, one per rank
+(no data-path collective; only the timing figures are reduced).  Run here as
+two gloo ranks on the CPU: the job figures are the slowest rank's time and
+the sum of the ranks' calls, and each rank's replica is its own random
+stream -- the oracle's pass on rank r equals a single-process run of the
+problem with request id r and differs from the other rank's."""
+import os
+import socket
+
+import numpy as np
+import pytest
+import torch.multiprocessing as mp
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, out):
+    import sys
+    import torch.distributed as dist
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    sys.path.insert(0, root)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    from oracle import oracle as O
+    from paper_1811_09711_gb300 import problems as P
+    t, calls = bench.job_throughput(10.0 + 5.0 * rank, 1000.0 * (rank + 1), world)
+    pr = bench.replica_problem(P.bw_gauss(), rank)
+    r = O.Oracle(pr).sample_pass(3000, 0, n_threads=1)
+    out.put((rank, t, calls, pr.request_id, r.integral, r.n_calls))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_replicas_over_gloo(oracle_mod):
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=300) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    (r0, t0, c0, id0, i0, n0), (r1, t1, c1, id1, i1, n1) = res
+    assert t0 == t1 == 15.0 and c0 == c1 == 3000.0  # max time, summed calls
+    assert (id0, id1) == (0, 1)
+    assert i0 != i1  # independent random streams
+    from paper_1811_09711_gb300 import problems as P
+    for rid, integral in ((0, i0), (1, i1)):
+        ref = oracle_mod.Oracle(P.bw_gauss().replace(request_id=rid)).sample_pass(3000, 0, n_threads=1)
+        assert ref.integral == integral
+
+
+def test_single_rank_is_identity():
+    import bench
+    assert bench.job_throughput(12.5, 7.0, 1) == (12.5, 7.0)
