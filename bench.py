@@ -165,11 +165,30 @@ def measured_traffic(kernel: str):
 
 
 def lookup_ops_per_call(pr) -> float:
-    """Algorithmic lane-operations per call charged to the roofline: the K*d
-    bin lookups of g(p), 8 lane-ops each (cell index 2, table probe 1, edge
-    probe + compare + select 3, density read + multiply 2).  Maps, integrand
-    and RNG are not charged, so the fraction is conservative."""
+    """The K*d bin lookups of g(p) alone, 8 lane-ops each (cell index 2,
+    table probe 1, edge probe + compare + select 3, density read + multiply 2)."""
     return 8.0 * pr.n_channels * pr.d
+
+
+def algorithmic_ops_per_call(pr) -> float:
+    """Algorithmic lane-operations of one call (what the method must compute,
+    not what a kernel happens to issue), charged to the roofline:
+      8 per bin lookup (K*d of them, as above);
+      15 per inverse map of a mapped coordinate of another channel (the
+        inverse map itself, its Jacobian factor, the matching peak's factor
+        and the coordinate's Gaussian exponent);
+      7 per channel for its terms of g and f (two multiply-adds, one exp2,
+        two multiplies, the exponent difference);
+      6 per coordinate for the forward map (bin index and fraction from the
+        random word, interpolation, density) and 2 for its d-value update;
+      60 per Philox4x32-10 block (ten rounds of two 32-bit multiplies, xors
+        and key updates) for the d words of the call;
+      10 for the weight and the channel sums.
+    For the collider-like problem (d = 14, K = 64, 188 mapped coordinates)
+    this is 10 798 lane-ops per call."""
+    K, d = pr.n_channels, pr.d
+    mapped = int(sum(int(x) for x in pr.channels.n_mapped))
+    return (8.0 * K * d + 15.0 * mapped + 7.0 * K + 8.0 * d + 60.0 * ((d + 3) // 4) + 10.0)
 
 
 def cpu_oracle_rate(pr, seconds: float, threads: int):
@@ -460,12 +479,14 @@ def run_gpu(args):
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     peak_tops = n_sm * 128 * sm_max * 1e6 / 1e12  # lane-ops/s: 4 schedulers x 32 lanes per SM
     k_ms = ks["sample_ms"] / max(ks["sample_launches"], 1)
-    ops = lookup_ops_per_call(pr) * (calls / max(args.steps, 1))
+    ops = algorithmic_ops_per_call(pr) * (calls / max(args.steps, 1))
     achieved = ops / (k_ms / 1e3) / 1e12
     kname = g.kernel_name()
     roof = {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "Tops/s",
             "frac": achieved / peak_tops, "traffic": measured_traffic(kname),
             "kernel": kname, "kernel_ms": k_ms,
+            "ops_per_call": algorithmic_ops_per_call(pr),
+            "frac_lookups_only": lookup_ops_per_call(pr) * (calls / max(args.steps, 1)) / (k_ms / 1e3) / 1e12 / peak_tops,
             "peak_source": f"{n_sm} SMs x 128 lanes x {sm_max:.0f} MHz ({src} max clock)"}
 
     res = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
