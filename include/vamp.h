@@ -208,6 +208,15 @@ vamp_status vamp_allocate(vamp_ctx *ctx, int64_t n_calls, int64_t *n_total);
  * generation kernel; vamp_kernel_stats returns the summed device time (ms)
  * and the launch counts since the last enable.  Off by default. */
 vamp_status vamp_profile(vamp_ctx *ctx, int32_t enable);
+
+/* Self-test of the device-side bounded wait that every staged-tile wait of
+ * the pass kernels uses: one CTA waits, with a limit of limit_cycles SM
+ * cycles (1 .. 2^31), for an mbarrier phase that nothing completes.  Returns
+ * VAMP_ERR_TIMEOUT when the wait gave up as designed (the device and every
+ * context stay usable), VAMP_OK if it was not armed, INVALID_ARG / OOM /
+ * CUDA otherwise; *waited_cycles (may be NULL) receives the cycles waited.
+ * Synchronises the device's legacy default stream. */
+vamp_status vamp_selftest_bounded_wait(int64_t limit_cycles, int64_t *waited_cycles);
 vamp_status vamp_kernel_stats(vamp_ctx *ctx, double *sample_ms, int64_t *sample_launches, double *gen_ms,
                               int64_t *gen_launches);
 

@@ -617,4 +617,23 @@ vamp_status vamp_pass_kernel_info(const vamp_ctx* c, int32_t* fp32, int32_t* cpt
     return VAMP_OK;
 }
 
+vamp_status vamp_selftest_bounded_wait(int64_t limit_cycles, int64_t* waited_cycles)
+{
+    if (limit_cycles < 1 || limit_cycles > (int64_t(1) << 31)) return VAMP_ERR_INVALID_ARG;
+    void* mem = nullptr;
+    if (cudaMalloc(&mem, 16) != cudaSuccess) return VAMP_ERR_OOM;
+    unsigned int* flag = static_cast<unsigned int*>(mem);
+    long long* cycles = reinterpret_cast<long long*>(static_cast<unsigned char*>(mem) + 8);
+    unsigned int h_flag = 0;
+    long long h_cycles = 0;
+    cudaError_t e = cudaMemset(mem, 0, 16);
+    if (e == cudaSuccess) e = vamp::launch_wait_selftest((long long)limit_cycles, flag, cycles, 0);
+    if (e == cudaSuccess) e = cudaMemcpy(&h_flag, flag, sizeof h_flag, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(&h_cycles, cycles, sizeof h_cycles, cudaMemcpyDeviceToHost);
+    cudaFree(mem);
+    if (e != cudaSuccess) return VAMP_ERR_CUDA;
+    if (waited_cycles) *waited_cycles = h_cycles;
+    return (h_flag & vamp::ERR_TIMEOUT) ? VAMP_ERR_TIMEOUT : VAMP_OK;
+}
+
 }  // extern "C"

@@ -608,14 +608,15 @@ __device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity)
     return ok != 0;
 }
 
-// Waits for phase `parity` of bar; gives up after ~2^31 SM cycles (about a
-// second) and returns false, so that no wait can hang the GPU.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity)
+// Waits for phase `parity` of bar; gives up after `limit` SM cycles (by
+// default 2^31, about a second) and returns false, so that no wait can hang
+// the GPU.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, long long limit = 1ll << 31)
 {
     if (mbar_test(bar, parity)) return true;
     const long long t0 = clock64();
     while (!mbar_test(bar, parity)) {
-        if (clock64() - t0 > (1ll << 31)) return false;
+        if (clock64() - t0 > limit) return false;
     }
     return true;
 }

@@ -141,5 +141,6 @@ cudaError_t launch_gen_prepare(const Params& P, cudaStream_t s);
 cudaError_t launch_gen_finish(const Params& P, const PassArgs& G, int64_t remaining, unsigned char* out,
                               cudaStream_t s);
 cudaError_t launch_eval(const Params& P, int fp32, const EvalArgs& A, cudaStream_t s);
+cudaError_t launch_wait_selftest(long long limit, unsigned int* flag, long long* cycles, cudaStream_t s);
 
 }  // namespace vamp

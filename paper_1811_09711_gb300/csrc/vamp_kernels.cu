@@ -541,6 +541,34 @@ cudaError_t launch_batch_after(const MultiArgs& M, cudaStream_t s)
 }
 
 // ---------------------------------------------------------------------------
+// self-test of the bounded wait: one CTA arms an mbarrier for a copy that is
+// never issued, waits with the pass kernels' wait routine and a short limit,
+// and records that it gave up (flag bit 0) and the cycles it waited
+// ---------------------------------------------------------------------------
+__global__ void k_wait_selftest(long long limit, unsigned int* flag, long long* cycles)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    const long long t0 = clock64();
+    const bool ok = mbar_wait_bounded(&bar, 0u, limit);  // nothing completes phase 0
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (!ok) atomicOr(flag, ERR_TIMEOUT);
+        *cycles = clock64() - t0;
+    }
+}
+
+cudaError_t launch_wait_selftest(long long limit, unsigned int* flag, long long* cycles, cudaStream_t s)
+{
+    k_wait_selftest<<<1, 64, 0, s>>>(limit, flag, cycles);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // host-side launchers
 // ---------------------------------------------------------------------------
 cudaError_t launch_begin_pass(const Params& P, int64_t N, cudaStream_t s)

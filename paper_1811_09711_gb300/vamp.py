@@ -144,6 +144,8 @@ def load():
         lib.vamp_server_load.restype = st
         lib.vamp_server_destroy.argtypes = [vp]
         lib.vamp_server_destroy.restype = None
+        lib.vamp_selftest_bounded_wait.argtypes = [i64, C.POINTER(i64)]
+        lib.vamp_selftest_bounded_wait.restype = st
         lib.vamp_destroy.argtypes = [vp]
         lib.vamp_destroy.restype = None
         lib.vamp_last_error.argtypes = [vp]
@@ -441,6 +443,14 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def selftest_bounded_wait(limit_cycles: int):
+    """vamp_selftest_bounded_wait: (status, cycles waited)."""
+    lib = load()
+    cyc = C.c_int64()
+    rc = lib.vamp_selftest_bounded_wait(int(limit_cycles), C.byref(cyc))
+    return rc, cyc.value
 
 
 def sample_pass_static(problem, precision: int, edges_ptr: int, alpha_ptr: int, shift_ptr: int,

@@ -146,3 +146,10 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert got[(cname, "size")] == C.sizeof(cls), cname
         for f, _ in cls._fields_:
             assert got[(cname, f)] == getattr(cls, f).offset, (cname, f)
+
+
+def test_selftest_bounded_wait_rejects_bad_limits(lib):
+    import ctypes as C
+    cyc = C.c_int64()
+    assert lib.vamp_selftest_bounded_wait(0, C.byref(cyc)) == V.VAMP_ERR_INVALID_ARG
+    assert lib.vamp_selftest_bounded_wait((1 << 31) + 1, C.byref(cyc)) == V.VAMP_ERR_INVALID_ARG
