@@ -205,12 +205,18 @@ template <> struct Prec<double> {
     {
         return __double_as_longlong(e) <= __double_as_longlong(x);
     }
-    // floor(x L) for x clamped to [0, 1): exact via round-toward-zero 1 + x
+    // floor(x L) for x clamped to [0, 1), from the bit pattern with integer
+    // operations only (the FP64 pipe is the scarce one): x = m 2^(e-52) with
+    // the 53-bit significand m, so floor(x 2^lshift) = m >> (52 - e - lshift)
     static __device__ __forceinline__ int cell(double x, int lshift)
     {
-        const double xc = fmin(fmax(x, 0.0), 0x1.fffffffffffffp-1);
-        const double y = __dadd_rz(xc, 1.0);
-        return (int)((unsigned long long)(__double_as_longlong(y) & 0xfffffffffffffll) >> (52 - lshift));
+        const long long b = __double_as_longlong(x);
+        if (b <= 0) return 0;                                    // x <= 0 (or -0)
+        if (b >= 0x3FF0000000000000ll) return (1 << lshift) - 1; // x >= 1
+        const int e = (int)(b >> 52) - 1023;                     // e <= -1
+        const int sh = 52 - e - lshift;
+        const unsigned long long m = (unsigned long long)(b & 0xFFFFFFFFFFFFFll) | (1ull << 52);
+        return sh >= 64 ? 0 : (int)(m >> sh);
     }
 };
 
