@@ -179,6 +179,20 @@ vamp_status vamp_get_state(vamp_ctx *ctx, double *edges, double *alpha, double *
  * strictly increasing from 0 to 1 on every row, α >= 0 with Σ α > 0.
  * Marks the context as having run a pass (so refine/generate are allowed).
  * Synchronises. */
+/* Checkpoint of the adaptation state (the analogue of the grid file that
+ * the paper's master writes after each iteration for restarts, §4.5): grids ξ,
+ * α, channel shifts, generation w_max and the history of passes that the
+ * iteration combination uses, as one self-describing host blob (magic
+ * "VAMPCKP1", d, K, n, precision, then FP64 arrays).  vamp_checkpoint_bytes
+ * gives the blob size (-1 on error; synchronises); vamp_checkpoint writes it
+ * to host_buf (bytes >= that size); vamp_restore loads a blob of the same
+ * (d, K, n) into a context (either precision: the master state is FP64),
+ * validating it as vamp_set_state does.  A run restored after iteration i
+ * continues as the uninterrupted run would (next pass: iteration i+1). */
+int64_t vamp_checkpoint_bytes(vamp_ctx *ctx);
+vamp_status vamp_checkpoint(vamp_ctx *ctx, void *host_buf, int64_t bytes);
+vamp_status vamp_restore(vamp_ctx *ctx, const void *host_buf, int64_t bytes);
+
 vamp_status vamp_set_state(vamp_ctx *ctx, const double *edges, const double *alpha,
                            const double *shift, double w_max);
 

@@ -524,6 +524,106 @@ vamp_status vamp_set_state(vamp_ctx* c, const double* edges, const double* alpha
     return VAMP_OK;
 }
 
+// ---- checkpoint / restore ----------------------------------------------------
+namespace {
+constexpr char CKP_MAGIC[8] = {'V', 'A', 'M', 'P', 'C', 'K', 'P', '1'};
+struct CkpHeader {
+    char magic[8];
+    int32_t d, K, n, precision;
+    int32_t n_hist, pad;
+    double w_max;
+};
+size_t ckp_bytes(int d, int K, int n, int n_hist)
+{
+    const size_t edges = (size_t)K * d * (n + 1);
+    return sizeof(CkpHeader) + 8 * (edges + 2 * (size_t)K + 2 * (size_t)n_hist) + 8 * (((size_t)n_hist * 4 + 7) / 8);
+}
+}  // namespace
+
+int64_t vamp_checkpoint_bytes(vamp_ctx* c)
+{
+    if (!c) return -1;
+    if (read_head(c) != VAMP_OK) return -1;
+    return (int64_t)ckp_bytes(c->d, c->K, c->n, c->h_head->n_hist);
+}
+
+vamp_status vamp_checkpoint(vamp_ctx* c, void* host_buf, int64_t bytes)
+{
+    if (!c) return VAMP_ERR_INVALID_ARG;
+    if (!host_buf) return fail(c, VAMP_ERR_INVALID_ARG, "host_buf is required");
+    DeviceGuard g(c->dev);
+    vamp_status s = read_head(c);
+    if (s != VAMP_OK) return s;
+    const int nh = c->h_head->n_hist;
+    if (bytes < (int64_t)ckp_bytes(c->d, c->K, c->n, nh)) return fail(c, VAMP_ERR_INVALID_ARG, "buffer too small");
+    CkpHeader h{};
+    std::memcpy(h.magic, CKP_MAGIC, 8);
+    h.d = c->d;
+    h.K = c->K;
+    h.n = c->n;
+    h.precision = c->fp32 ? VAMP_PREC_FP32_EVAL : VAMP_PREC_FP64;
+    h.n_hist = nh;
+    h.w_max = c->h_head->wmax_gen;
+    unsigned char* o = static_cast<unsigned char*>(host_buf);
+    std::memcpy(o, &h, sizeof h);
+    o += sizeof h;
+    const size_t ne = (size_t)c->K * c->d * (c->n + 1);
+    const Params& P = c->prm;
+    VAMP_CK(c, cudaMemcpyAsync(o, P.edges64, ne * 8, cudaMemcpyDeviceToHost, c->stream));
+    o += ne * 8;
+    VAMP_CK(c, cudaMemcpyAsync(o, P.alpha, (size_t)c->K * 8, cudaMemcpyDeviceToHost, c->stream));
+    o += (size_t)c->K * 8;
+    VAMP_CK(c, cudaMemcpyAsync(o, P.shift, (size_t)c->K * 8, cudaMemcpyDeviceToHost, c->stream));
+    o += (size_t)c->K * 8;
+    if (nh > 0) {
+        VAMP_CK(c, cudaMemcpyAsync(o, P.sc->hist_I, (size_t)nh * 8, cudaMemcpyDeviceToHost, c->stream));
+        o += (size_t)nh * 8;
+        VAMP_CK(c, cudaMemcpyAsync(o, P.sc->hist_V, (size_t)nh * 8, cudaMemcpyDeviceToHost, c->stream));
+        o += (size_t)nh * 8;
+        VAMP_CK(c, cudaMemcpyAsync(o, P.sc->hist_comb, (size_t)nh * 4, cudaMemcpyDeviceToHost, c->stream));
+    }
+    VAMP_CK(c, cudaStreamSynchronize(c->stream));
+    return VAMP_OK;
+}
+
+vamp_status vamp_restore(vamp_ctx* c, const void* host_buf, int64_t bytes)
+{
+    if (!c) return VAMP_ERR_INVALID_ARG;
+    if (!host_buf || bytes < (int64_t)sizeof(CkpHeader)) return fail(c, VAMP_ERR_INVALID_ARG, "no checkpoint");
+    CkpHeader h;
+    std::memcpy(&h, host_buf, sizeof h);
+    if (std::memcmp(h.magic, CKP_MAGIC, 8) != 0) return fail(c, VAMP_ERR_INVALID_ARG, "not a checkpoint");
+    if (h.d != c->d || h.K != c->K || h.n != c->n)
+        return fail(c, VAMP_ERR_INVALID_ARG, "checkpoint of another shape (d, K, n)");
+    if (h.n_hist < 0 || h.n_hist > 1024 || bytes < (int64_t)ckp_bytes(h.d, h.K, h.n, h.n_hist))
+        return fail(c, VAMP_ERR_INVALID_ARG, "truncated checkpoint");
+    const unsigned char* o = static_cast<const unsigned char*>(host_buf) + sizeof h;
+    const size_t ne = (size_t)c->K * c->d * (c->n + 1);
+    std::vector<double> edges(ne), alpha(c->K), shift(c->K);
+    std::memcpy(edges.data(), o, ne * 8);
+    o += ne * 8;
+    std::memcpy(alpha.data(), o, (size_t)c->K * 8);
+    o += (size_t)c->K * 8;
+    std::memcpy(shift.data(), o, (size_t)c->K * 8);
+    o += (size_t)c->K * 8;
+    // grids, α, shifts and w_max through the validating state upload
+    vamp_status s = vamp_set_state(c, edges.data(), alpha.data(), shift.data(), h.w_max);
+    if (s != VAMP_OK) return s;
+    DeviceGuard g(c->dev);
+    const Params& P = c->prm;
+    if (h.n_hist > 0) {
+        VAMP_CK(c, cudaMemcpyAsync(P.sc->hist_I, o, (size_t)h.n_hist * 8, cudaMemcpyHostToDevice, c->stream));
+        o += (size_t)h.n_hist * 8;
+        VAMP_CK(c, cudaMemcpyAsync(P.sc->hist_V, o, (size_t)h.n_hist * 8, cudaMemcpyHostToDevice, c->stream));
+        o += (size_t)h.n_hist * 8;
+        VAMP_CK(c, cudaMemcpyAsync(P.sc->hist_comb, o, (size_t)h.n_hist * 4, cudaMemcpyHostToDevice, c->stream));
+    }
+    const int32_t nh = h.n_hist;
+    VAMP_CK(c, cudaMemcpyAsync(&P.sc->n_hist, &nh, sizeof nh, cudaMemcpyHostToDevice, c->stream));
+    VAMP_CK(c, cudaStreamSynchronize(c->stream));
+    return VAMP_OK;
+}
+
 vamp_status vamp_get_pass(vamp_ctx* c, double* D, double* Ic, double* Vc, int64_t* Nc)
 {
     if (!c) return VAMP_ERR_INVALID_ARG;

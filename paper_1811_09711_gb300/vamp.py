@@ -144,6 +144,12 @@ def load():
         lib.vamp_server_load.restype = st
         lib.vamp_server_destroy.argtypes = [vp]
         lib.vamp_server_destroy.restype = None
+        lib.vamp_checkpoint_bytes.argtypes = [vp]
+        lib.vamp_checkpoint_bytes.restype = i64
+        lib.vamp_checkpoint.argtypes = [vp, vp, i64]
+        lib.vamp_checkpoint.restype = st
+        lib.vamp_restore.argtypes = [vp, vp, i64]
+        lib.vamp_restore.restype = st
         lib.vamp_selftest_bounded_wait.argtypes = [i64, C.POINTER(i64)]
         lib.vamp_selftest_bounded_wait.restype = st
         lib.vamp_destroy.argtypes = [vp]
@@ -306,6 +312,19 @@ class Vamp:
         a = None if alpha is None else np.ascontiguousarray(alpha, np.float64)
         s = None if shift is None else np.ascontiguousarray(shift, np.float64)
         self._check(self.lib.vamp_set_state(self.h, _ptr(e), _ptr(a), _ptr(s), float(w_max)))
+
+    def checkpoint(self) -> bytes:
+        """The adaptation state as a self-describing blob (vamp_checkpoint)."""
+        n = int(self.lib.vamp_checkpoint_bytes(self.h))
+        if n < 0:
+            raise VampError(VAMP_ERR_CUDA, self.lib.vamp_last_error(self.h).decode())
+        buf = C.create_string_buffer(n)
+        self._check(self.lib.vamp_checkpoint(self.h, buf, n))
+        return buf.raw
+
+    def restore(self, blob: bytes):
+        buf = C.create_string_buffer(bytes(blob), len(blob))
+        self._check(self.lib.vamp_restore(self.h, buf, len(blob)))
 
     def get_pass(self):
         D = np.zeros((self.K, self.d, self.n), np.float64)
