@@ -56,6 +56,7 @@ class _Problem(C.Structure):
         ("n_min", C.c_int64),
         ("smooth", C.c_int32), ("omega_mode", C.c_int32),
         ("gen_batch", C.c_int64),
+        ("stratified", C.c_int32),
     ]
 
 
@@ -105,6 +106,8 @@ def _load():
             lib.or_alpha_update_raw.restype = None
             lib.or_allocate_raw.argtypes = [C.c_int, vp, i64, i64, vp, vp]
             lib.or_allocate_raw.restype = i64
+            lib.or_strat_cells_per_axis.argtypes = [i64, C.c_int]
+            lib.or_strat_cells_per_axis.restype = i64
             _lib = lib
     return _lib
 
@@ -144,6 +147,11 @@ def alpha_update(alpha, omega, Ic, Nc, beta: float = 0.5) -> np.ndarray:
     lib.or_alpha_update_raw(int(a.shape[0]), _ptr(a), _ptr(om), _ptr(ic), _ptr(nc), float(beta),
                             _ptr(out))
     return out
+
+
+def strat_cells_per_axis(n_calls: int, d: int) -> int:
+    """R16: the largest m (<= 2^20) with 2 m^d <= n_calls."""
+    return int(_load().or_strat_cells_per_axis(int(n_calls), int(d)))
 
 
 def allocate(alpha, n_calls: int, n_min: int = 10):
@@ -197,7 +205,7 @@ class Oracle:
                       _ptr(k[10]).value, float(pr.gauss_sigma), float(pr.gauss_centre),
                       int(pr.gauss_norm), int(pr.seed) & (2**64 - 1), int(pr.request_id),
                       float(pr.grid_alpha), float(pr.beta), int(pr.n_min), int(pr.smooth),
-                      int(pr.omega_mode), int(pr.gen_batch))
+                      int(pr.omega_mode), int(pr.gen_batch), int(getattr(pr, "stratified", 0)))
         status = C.c_int(0)
         self.h = self.lib.or_create(C.byref(st), C.byref(status))
         if not self.h:

@@ -43,6 +43,18 @@
  *   R13 per-channel sums shifted by the previous pass's channel mean.
  *   R14 synthetic integrand factors normalised on [0,1] (or the real line).
  *   R15 power map p = x^5 with p clamped to >= the smallest normal double.
+ *   R16 pseudo-stratified sampling (§3.3, optional): per channel, n_r cells
+ *       per r axis, the largest m (<= 2^20) with 2 m^d <= N_c; C = n_r^d
+ *       cells; s = floor(N_c / C) points per cell; the channel samples
+ *       N_c = s C calls.  Local call l lies in cell floor(l / s), whose
+ *       base-n_r digits a_k place r_k = (a_k + u_k) / n_r; the forward bin
+ *       and fraction come from the integer (2^33 a_k + 2X + 1) n over
+ *       n_r 2^33 (R10 is the case n_r = 1).  Generation stays importance
+ *       sampling.
+ *   R17 stratified variance: the per-call variance entering σ² (R8) and the
+ *       α update is the mean over the channel's cells of the cells' sample
+ *       variances, [Σ d² - Σ_cells (Σ_cell d)² / s] / (C (s - 1)) with
+ *       d = w - s_c (R13); 0 for s < 2.
  */
 #include <float.h>
 #include <math.h>
@@ -75,6 +87,7 @@ typedef struct {
     int64_t n_min;
     int32_t smooth, omega_mode;
     int64_t gen_batch;
+    int32_t stratified;                          /* R16 */
 } or_problem;
 
 /* Neumaier-compensated sum. */
@@ -114,6 +127,8 @@ typedef struct or_ctx {
     double *alpha;   /* K */
     double *shift;   /* K: s_c (R13) */
     int64_t *Nc, *Pc; /* K, K+1 */
+    int stratified;   /* R16 */
+    int64_t *nr, *spc, *Cc; /* K each: cells per axis, points per cell, cells */
     int64_t n_total;
     double *D;       /* K*d*n */
     double *Ic, *Vc, *Wc; /* K */
@@ -316,17 +331,27 @@ static double g_of_p(const or_ctx *o, int own, const double *p, double g_own, do
 
 /* One call of channel c from its random words: §3.5 work order.
  * Returns w = f(p)/g(p); fills x (channel coordinates), p, forward bins. */
-static double eval_call(const or_ctx *o, int c, const uint32_t *X, double *x, double *p,
-                        int *jf, int *bins_all, double *f_out, double *g_out)
+static double eval_call(const or_ctx *o, int c, const uint32_t *X, const int64_t *digit, int64_t nr,
+                        double *x, double *p, int *jf, int *bins_all, double *f_out, double *g_out)
 {
     const double *e;
     double gc = 1.0;
     /* x_c = G_c^{-1}(r): bin index and in-bin fraction from the integer
-     * (2X+1) n (R10), linear inside the bin (§3.2). */
+     * (2X+1) n (R10), or (2^33 a_k + 2X + 1) n over n_r 2^33 in a
+     * stratification cell with digits a_k (R16); linear inside the bin (§3.2). */
     for (int k = 0; k < o->d; ++k) {
-        uint64_t t = (2ull * X[k] + 1ull) * (uint64_t)o->n;
-        int j = (int)(t >> 33);
-        double fr = (double)(t & ((1ull << 33) - 1ull)) * 0x1p-33;
+        int j;
+        double fr;
+        if (digit) {
+            const uint64_t den = (uint64_t)nr << 33;
+            const uint64_t t = (((uint64_t)digit[k] << 33) + 2ull * X[k] + 1ull) * (uint64_t)o->n;
+            j = (int)(t / den);
+            fr = (double)(t % den) / (double)den;
+        } else {
+            uint64_t t = (2ull * X[k] + 1ull) * (uint64_t)o->n;
+            j = (int)(t >> 33);
+            fr = (double)(t & ((1ull << 33) - 1ull)) * 0x1p-33;
+        }
         e = edge_row(o, c, k);
         double w = e[j + 1] - e[j];
         x[k] = e[j] + fr * w;
@@ -387,6 +412,7 @@ void or_destroy(or_ctx *o)
     if (!o) return;
     free(o->ch); free(o->pk); free(o->pk_w); free(o->edges); free(o->alpha); free(o->shift);
     free(o->Nc); free(o->Pc); free(o->D); free(o->Ic); free(o->Vc); free(o->Wc);
+    free(o->nr); free(o->spc); free(o->Cc);
     free(o);
 }
 
@@ -411,8 +437,14 @@ or_ctx *or_create(const or_problem *pr, int *status)
     o->Ic = calloc(o->K, sizeof(double));
     o->Vc = calloc(o->K, sizeof(double));
     o->Wc = calloc(o->K, sizeof(double));
+    o->nr = calloc(o->K, sizeof(int64_t));
+    o->spc = calloc(o->K, sizeof(int64_t));
+    o->Cc = calloc(o->K, sizeof(int64_t));
     if (!o->ch || !o->pk || !o->pk_w || !o->edges || !o->D || !o->alpha || !o->shift || !o->Nc ||
-        !o->Pc || !o->Ic || !o->Vc || !o->Wc) { or_destroy(o); *status = OR_ERR_MEM; return NULL; }
+        !o->Pc || !o->Ic || !o->Vc || !o->Wc || !o->nr || !o->spc || !o->Cc) {
+        or_destroy(o); *status = OR_ERR_MEM; return NULL;
+    }
+    o->stratified = pr->stratified ? 1 : 0;
     if (load_maps(o->ch, o->K, o->d, pr->ch_nmap, pr->ch_coord, pr->ch_kind, pr->ch_a, pr->ch_b) ||
         load_maps(o->pk, o->P, o->d, pr->pk_nmap, pr->pk_coord, pr->pk_kind, pr->pk_a, pr->pk_b)) {
         or_destroy(o); return NULL;
@@ -461,9 +493,40 @@ int64_t or_allocate_raw(int K, const double *alpha, int64_t N, int64_t n_min, in
     return Pc[K];
 }
 
+/* R16: the largest m in [1, 2^20] with 2 m^d <= N (1 if N < 2^(d+1)). */
+int64_t or_strat_cells_per_axis(int64_t N, int d)
+{
+    int64_t lo = 1, hi = 1 << 20;
+    while (lo < hi) {
+        int64_t mid = (lo + hi + 1) / 2, prod = 2;
+        for (int k = 0; k < d && prod <= N; ++k) {
+            if (prod > N / mid) { prod = N + 1; break; }
+            prod *= mid;
+        }
+        if (prod <= N) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
 int64_t or_allocate(or_ctx *o, int64_t N)
 {
     o->n_total = or_allocate_raw(o->K, o->alpha, N, o->n_min, o->Nc, o->Pc);
+    if (o->stratified) {
+        o->Pc[0] = 0;
+        for (int c = 0; c < o->K; ++c) {
+            int64_t m = 1, C = 1, s = o->Nc[c];
+            if (o->Nc[c] >= 2) {
+                m = or_strat_cells_per_axis(o->Nc[c], o->d);
+                C = 1;
+                for (int k = 0; k < o->d; ++k) C *= m;
+                s = o->Nc[c] / C;
+            }
+            o->nr[c] = m; o->Cc[c] = C; o->spc[c] = s;
+            o->Nc[c] = s * C;
+            o->Pc[c + 1] = o->Pc[c] + o->Nc[c];
+        }
+        o->n_total = o->Pc[o->K];
+    }
     return o->n_total;
 }
 
@@ -473,34 +536,60 @@ int64_t or_allocate(or_ctx *o, int64_t N)
 typedef struct {
     const or_ctx *o;
     uint32_t iteration;
-    int64_t i0, i1;
-    ksum *S1, *S2, *D;
+    int64_t i0, i1;           /* calls (importance) or cells (stratified) */
+    const int64_t *cell_off;  /* K+1: first cell of each channel (stratified) */
+    ksum *S1, *S2, *D, *Q;    /* Q: Σ_cells (Σ_cell d)^2 per channel (R17) */
     double wmax;
     int bad;
 } pass_part;
+
+/* One call: weight, shifted sums, d-values, w_max. */
+static double pass_call(pass_part *pp, int c, int64_t i, const int64_t *digit, uint32_t *X, double *x,
+                        double *p, int *jf)
+{
+    const or_ctx *o = pp->o;
+    const int d = o->d, n = o->n;
+    call_words(o, (uint32_t)i, pp->iteration, d, X);
+    double w = eval_call(o, c, X, digit, digit ? o->nr[c] : 0, x, p, jf, NULL, NULL, NULL);
+    if (!isfinite(w)) { pp->bad = 1; w = 0.0; }
+    double dv = w - o->shift[c];
+    ks_add(&pp->S1[c], dv);
+    ks_add(&pp->S2[c], dv * dv);
+    double w2 = w * w;
+    for (int k = 0; k < d; ++k) ks_add(&pp->D[((size_t)c * d + k) * n + jf[k]], w2);
+    if (w > pp->wmax) pp->wmax = w;
+    return dv;
+}
 
 static void *pass_worker(void *arg)
 {
     pass_part *pp = arg;
     const or_ctx *o = pp->o;
-    int d = o->d, n = o->n;
-    int nw = d;
     uint32_t X[OR_MAX_D + 4];
     double x[OR_MAX_D], p[OR_MAX_D];
     int jf[OR_MAX_D];
     int c = 0;
-    while (c < o->K && o->Pc[c + 1] <= pp->i0) ++c;
-    for (int64_t i = pp->i0; i < pp->i1; ++i) {
-        while (o->Pc[c + 1] <= i) ++c;
-        call_words(o, (uint32_t)i, pp->iteration, nw, X);
-        double w = eval_call(o, c, X, x, p, jf, NULL, NULL, NULL);
-        if (!isfinite(w)) { pp->bad = 1; w = 0.0; }
-        double dv = w - o->shift[c];
-        ks_add(&pp->S1[c], dv);
-        ks_add(&pp->S2[c], dv * dv);
-        double w2 = w * w;
-        for (int k = 0; k < d; ++k) ks_add(&pp->D[((size_t)c * d + k) * n + jf[k]], w2);
-        if (w > pp->wmax) pp->wmax = w;
+    if (!o->stratified) {
+        while (c < o->K && o->Pc[c + 1] <= pp->i0) ++c;
+        for (int64_t i = pp->i0; i < pp->i1; ++i) {
+            while (o->Pc[c + 1] <= i) ++c;
+            pass_call(pp, c, i, NULL, X, x, p, jf);
+        }
+        return NULL;
+    }
+    /* R16/R17: whole cells; the s calls of a cell are consecutive */
+    int64_t digit[OR_MAX_D];
+    while (c < o->K && pp->cell_off[c + 1] <= pp->i0) ++c;
+    for (int64_t q = pp->i0; q < pp->i1; ++q) {
+        while (pp->cell_off[c + 1] <= q) ++c;
+        const int64_t l = q - pp->cell_off[c];
+        int64_t rest = l;
+        for (int k = 0; k < o->d; ++k) { digit[k] = rest % o->nr[c]; rest /= o->nr[c]; }
+        ksum cs = {0, 0};
+        for (int64_t m = 0; m < o->spc[c]; ++m)
+            ks_add(&cs, pass_call(pp, c, o->Pc[c] + l * o->spc[c] + m, digit, X, x, p, jf));
+        const double v = ks_val(&cs);
+        ks_add(&pp->Q[c], v * v);
     }
     return NULL;
 }
@@ -551,17 +640,22 @@ int or_sample_pass(or_ctx *o, int64_t N, uint32_t iteration, int combine, int n_
     if ((int64_t)n_threads > Nt) n_threads = (int)(Nt > 0 ? Nt : 1);
     pass_part *parts = calloc(n_threads, sizeof *parts);
     pthread_t *th = calloc(n_threads, sizeof *th);
+    int64_t *cell_off = calloc(K + 1, sizeof(int64_t));
+    for (int c = 0; c < K; ++c) cell_off[c + 1] = cell_off[c] + (o->stratified ? o->Cc[c] : 0);
+    const int64_t units = o->stratified ? cell_off[K] : Nt;  /* split by cells when stratified */
     int rc = OR_OK;
     for (int t = 0; t < n_threads; ++t) {
         parts[t].o = o;
         parts[t].iteration = iteration;
-        parts[t].i0 = Nt * t / n_threads;
-        parts[t].i1 = Nt * (t + 1) / n_threads;
+        parts[t].i0 = units * t / n_threads;
+        parts[t].i1 = units * (t + 1) / n_threads;
+        parts[t].cell_off = cell_off;
         parts[t].S1 = calloc(K, sizeof(ksum));
         parts[t].S2 = calloc(K, sizeof(ksum));
+        parts[t].Q = calloc(K, sizeof(ksum));
         parts[t].D = calloc(nd, sizeof(ksum));
         parts[t].wmax = 0.0;
-        if (!parts[t].S1 || !parts[t].S2 || !parts[t].D) rc = OR_ERR_MEM;
+        if (!parts[t].S1 || !parts[t].S2 || !parts[t].Q || !parts[t].D) rc = OR_ERR_MEM;
     }
     if (rc == OR_OK) {
         if (n_threads == 1) pass_worker(&parts[0]);
@@ -573,10 +667,11 @@ int or_sample_pass(or_ctx *o, int64_t N, uint32_t iteration, int combine, int n_
         double wmax = 0.0;
         int bad = 0;
         for (int c = 0; c < K; ++c) {
-            ksum s1 = {0, 0}, s2 = {0, 0};
+            ksum s1 = {0, 0}, s2 = {0, 0}, qq = {0, 0};
             for (int t = 0; t < n_threads; ++t) {
                 ks_add(&s1, parts[t].S1[c].s); ks_add(&s1, parts[t].S1[c].c);
                 ks_add(&s2, parts[t].S2[c].s); ks_add(&s2, parts[t].S2[c].c);
+                ks_add(&qq, parts[t].Q[c].s); ks_add(&qq, parts[t].Q[c].c);
             }
             double Nc = (double)o->Nc[c];
             if (o->Nc[c] == 0) { o->Ic[c] = o->Vc[c] = o->Wc[c] = 0.0; continue; }
@@ -584,7 +679,13 @@ int or_sample_pass(or_ctx *o, int64_t N, uint32_t iteration, int combine, int n_
             /* Eqs. 10, 11 per channel, on sums shifted by s_c (R13). */
             o->Ic[c] = o->shift[c] + m1;
             double V = 0.0;
-            if (o->Nc[c] > 1) V = (m2 - m1 * m1) * Nc / (Nc - 1.0);
+            if (!o->stratified) {
+                if (o->Nc[c] > 1) V = (m2 - m1 * m1) * Nc / (Nc - 1.0);
+            } else if (o->spc[c] >= 2) {
+                /* R17: mean over cells of the cell sample variances */
+                const double s = (double)o->spc[c];
+                V = (ks_val(&s2) - ks_val(&qq) / s) / ((double)o->Cc[c] * (s - 1.0));
+            }
             if (V < 0.0) V = 0.0;
             o->Vc[c] = V;
             o->Wc[c] = (m2 - m1 * m1) + o->Ic[c] * o->Ic[c];
@@ -625,8 +726,10 @@ int or_sample_pass(or_ctx *o, int64_t N, uint32_t iteration, int combine, int n_
         out[7] = o->comb_chi2;
         if (bad) rc = OR_ERR_NUMERIC;
     }
-    for (int t = 0; t < n_threads; ++t) { free(parts[t].S1); free(parts[t].S2); free(parts[t].D); }
-    free(parts); free(th);
+    for (int t = 0; t < n_threads; ++t) {
+        free(parts[t].S1); free(parts[t].S2); free(parts[t].Q); free(parts[t].D);
+    }
+    free(parts); free(th); free(cell_off);
     return rc;
 }
 
@@ -765,7 +868,7 @@ int or_generate(or_ctx *o, int64_t n_events, uint32_t gen_id, float *p_out, doub
         for (int64_t i = 0; i < o->gen_batch; ++i) {
             call_words(o, (uint32_t)i, field, d + 2, X);
             int c = choose_channel(o, A, unif(X[d]));
-            double w = eval_call(o, c, X, x, p, jf, NULL, NULL, NULL);
+            double w = eval_call(o, c, X, NULL, 0, x, p, jf, NULL, NULL, NULL);
             if (!isfinite(w)) { rc = OR_ERR_NUMERIC; w = 0.0; }
             if (w > bmax) bmax = w;
             if (written < n_events) {
@@ -801,12 +904,19 @@ int or_eval_call(const or_ctx *o, int mode, uint32_t field, uint32_t call, doubl
     int jfi[OR_MAX_D];
     int *ball = NULL;
     if (bins_all) ball = malloc((size_t)o->K * d * sizeof(int));
+    int64_t digit[OR_MAX_D];
+    int strat = 0;
     if (mode == 0) {
         if ((int64_t)call >= o->n_total) { free(ball); return OR_ERR_ARG; }
         c = 0;
         while (o->Pc[c + 1] <= (int64_t)call) ++c;
         call_words(o, call, field, d, X);
         if (words) for (int k = 0; k < d; ++k) words[k] = X[k];
+        if (o->stratified) {
+            int64_t rest = ((int64_t)call - o->Pc[c]) / o->spc[c];
+            for (int k = 0; k < d; ++k) { digit[k] = rest % o->nr[c]; rest /= o->nr[c]; }
+            strat = 1;
+        }
     } else {
         double *A = malloc(o->K * sizeof(double));
         double acc = 0.0;
@@ -817,7 +927,7 @@ int or_eval_call(const or_ctx *o, int mode, uint32_t field, uint32_t call, doubl
         free(A);
     }
     double f, g;
-    double w = eval_call(o, c, X, x, p, jfi, ball, &f, &g);
+    double w = eval_call(o, c, X, strat ? digit : NULL, strat ? o->nr[c] : 0, x, p, jfi, ball, &f, &g);
     for (int k = 0; k < d; ++k) jf[k] = jfi[k];
     if (bins_all) for (int q = 0; q < o->K * d; ++q) bins_all[q] = ball[q];
     free(ball);

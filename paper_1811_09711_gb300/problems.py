@@ -102,6 +102,7 @@ class Problem:
     adapt_alpha: bool = True
     combine_from: int = 0     # first iteration entering the combination
     n_events: int = 0
+    stratified: int = 0       # 1: pseudo-stratified sampling in r space (§3.3)
 
     @property
     def n_channels(self) -> int:

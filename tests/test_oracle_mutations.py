@@ -63,17 +63,31 @@ MUTATIONS = [
      "double tgt = (1.0 - u) * A[o->K - 1];", "channel_choice_is_inverse_cdf"),
     ("accept_inverted", "if (unif(X[d + 1]) * wm < w) {", "if (unif(X[d + 1]) * wm > w) {",
      "generation_brute_force"),
+    # pseudo-stratified mode (R16, R17): pins in test_oracle_stratified.py
+    ("strat_variance_no_bessel", "V = (ks_val(&s2) - ks_val(&qq) / s) / ((double)o->Cc[c] * (s - 1.0));",
+     "V = (ks_val(&s2) - ks_val(&qq) / s) / ((double)o->Cc[c] * s);",
+     "error_estimate_consistent", "test_oracle_stratified.py"),
+    ("strat_cell_sum_not_squared", "ks_add(&pp->Q[c], v * v);", "ks_add(&pp->Q[c], v);",
+     "zero_variance", "test_oracle_stratified.py"),
+    ("strat_digits_not_shifted",
+     "for (int k = 0; k < o->d; ++k) { digit[k] = rest % o->nr[c]; rest /= o->nr[c]; }\n        ksum cs",
+     "for (int k = 0; k < o->d; ++k) { digit[k] = rest % o->nr[c]; }\n        ksum cs",
+     "unbiased_and_error", "test_oracle_stratified.py"),
+    ("strat_fraction_denominator", "fr = (double)(t % den) / (double)den;", "fr = (double)(t % den) / 0x1p33;",
+     "points_lie", "test_oracle_stratified.py"),
 ]
 
 
-@pytest.mark.parametrize("name,old,new,selector", MUTATIONS, ids=[m[0] for m in MUTATIONS])
-def test_planted_mistake_is_caught(tmp_path, name, old, new, selector):
+@pytest.mark.parametrize("name,old,new,selector,pins",
+                         [m if len(m) == 5 else m + ("test_oracle_pins.py",) for m in MUTATIONS],
+                         ids=[m[0] for m in MUTATIONS])
+def test_planted_mistake_is_caught(tmp_path, name, old, new, selector, pins):
     src = open(SRC).read()
     assert src.count(old) >= 1, f"mutation site of {name} not found"
     msrc = tmp_path / "vamp_oracle_mut.c"
     msrc.write_text(src.replace(old, new, 1))
     env = dict(os.environ, VAMP_ORACLE_SRC=str(msrc), VAMP_ORACLE_LIB=str(tmp_path / "libmut.so"))
-    r = subprocess.run([sys.executable, "-m", "pytest", os.path.join(ROOT, "tests", "test_oracle_pins.py"),
+    r = subprocess.run([sys.executable, "-m", "pytest", os.path.join(ROOT, "tests", pins),
                         "-x", "-q", "-p", "no:cacheprovider", "-k", selector],
                        env=env, capture_output=True, text=True, timeout=600, cwd=ROOT)
     assert "passed" in r.stdout or "failed" in r.stdout, r.stdout + r.stderr
