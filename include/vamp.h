@@ -105,6 +105,12 @@ typedef struct {
     int64_t gen_batch;          /* calls per generation batch (0 = 2^20), <= 2^24 */
     int32_t combine_from;       /* passes with iteration >= this enter the combination */
     int32_t precision;          /* vamp_precision */
+    int32_t stratified;         /* 1: integration passes sample pseudo-stratified in r space (§3.3):
+                                   per channel n_r = the largest m (<= 2^20) with 2 m^d <= N_c cells
+                                   per axis, s = floor(N_c / n_r^d) calls per cell, N_c = s n_r^d;
+                                   the per-call variance is the mean of the cells' sample variances.
+                                   Generation stays importance sampling.  Contexts only (batches and
+                                   servers reject it). */
 } vamp_config;
 
 /* Result of one sampling pass (§3.1 Eqs. 10-11 per channel, Eq. 23 overall).

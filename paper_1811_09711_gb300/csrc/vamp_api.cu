@@ -35,6 +35,7 @@ struct vamp_ctx {
     size_t smem_gen = 0;       // ... of the generation pass kernel
     const PassVariant* var = nullptr;  // pass kernels in use
     int tuned = 0;             // var was chosen by timing (first sampling pass)
+    int64_t cell_cap = 0;      // cells the stratified-pass cell sums hold
     int grid_pass = 0;         // persistent grid of the integration pass kernel
     int grid_gen = 0;          // resident CTAs of the generation pass kernel
     int have_pass = 0;
@@ -161,7 +162,7 @@ vamp_status use_variant(vamp_ctx* c, const PassVariant* v)
 
 vamp_status choose_variant(vamp_ctx* c, int64_t n_calls)
 {
-    const std::vector<const PassVariant*> cand = vamp::pass_candidates(c->fp32, c->d, c->n);
+    const std::vector<const PassVariant*> cand = vamp::pass_candidates(c->fp32, c->d, c->n, c->prm.stratified);
     if (cand.empty()) return fail(c, VAMP_ERR_INVALID_ARG, "no pass kernel for this shape");
     for (const PassVariant* v : cand) {
         const VariantShape s = shape_of(c, v);
@@ -257,6 +258,7 @@ void vamp_destroy(vamp_ctx* c)
         DeviceGuard g(c->dev);
         if (c->stream) cudaStreamSynchronize(c->stream);
         cudaFree(c->arena);
+        cudaFree(c->prm.cellsum);
         cudaFree(c->g_staging);
         cudaFree(c->g_callidx);
         cudaFree(c->g_counts);
@@ -321,7 +323,7 @@ vamp_status vamp_create(const vamp_config* cfg, void* cuda_stream, vamp_ctx** ou
         CREATE_CK(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->dev));
         // until the first pass picks by timing: the first candidate (the
         // shape-specialised kernel if there is one)
-        const std::vector<const PassVariant*> cand = vamp::pass_candidates(c->fp32, c->d, c->n);
+        const std::vector<const PassVariant*> cand = vamp::pass_candidates(c->fp32, c->d, c->n, c->prm.stratified);
         if (cand.empty()) { st = fail(c, VAMP_ERR_INVALID_ARG, "no pass kernel for this shape"); goto create_fail; }
         st = use_variant(c, cand[0]);
         if (st != VAMP_OK) goto create_fail;
@@ -356,6 +358,19 @@ vamp_status vamp_sample_pass(vamp_ctx* c, int64_t n_calls, uint32_t iteration, v
     if (n_calls + (int64_t)c->K * c->prm.n_min > int64_t(0xffffffff))
         return fail(c, VAMP_ERR_INVALID_ARG, "too many calls for a 32-bit call counter");
     DeviceGuard g(c->dev);
+    // stratified passes: cell sums for at most (N + K n_min) / 2 cells (two
+    // calls or more per cell), grown on demand
+    const int64_t max_cells = c->prm.stratified ? (n_calls + (int64_t)c->K * c->prm.n_min) / 2 + c->K : 0;
+    if (max_cells > c->cell_cap) {
+        cudaFree(c->prm.cellsum);
+        c->prm.cellsum = nullptr;
+        c->cell_cap = 0;
+        if (cudaMalloc(&c->prm.cellsum, (size_t)max_cells * 8) != cudaSuccess) {
+            c->prm.cellsum = nullptr;
+            return fail(c, VAMP_ERR_OOM, "cell sums of a stratified pass");
+        }
+        c->cell_cap = max_cells;
+    }
     if (!c->tuned) {
         const vamp_status ts = choose_variant(c, n_calls);
         if (ts != VAMP_OK) return ts;
@@ -364,10 +379,12 @@ vamp_status vamp_sample_pass(vamp_ctx* c, int64_t n_calls, uint32_t iteration, v
     const Params& P = c->prm;
     VAMP_CK(c, cudaMemsetAsync(P.D, 0, (size_t)c->K * c->d * c->n * 8, c->stream));
     VAMP_CK(c, cudaMemsetAsync(P.csum, 0, (size_t)2 * c->K * 8, c->stream));
+    if (P.stratified) VAMP_CK(c, cudaMemsetAsync(P.cellsum, 0, (size_t)max_cells * 8, c->stream));
     VAMP_CK(c, vamp::launch_begin_pass(P, n_calls, c->stream));
     if (c->prof) VAMP_CK(c, cudaEventRecord(c->ev[0], c->stream));
     VAMP_CK(c, c->var->launch(P, 0, pass_args(c, iteration), c->grid_pass, c->smem_pass, c->stream));
     if (c->prof) VAMP_CK(c, cudaEventRecord(c->ev[1], c->stream));
+    if (P.stratified) VAMP_CK(c, vamp::launch_strat_q(P, c->stream));
     VAMP_CK(c, vamp::launch_finish_pass(P, (int)iteration >= c->combine_from ? 1 : 0, c->stream));
     vamp_status s = read_head(c);
     if (s != VAMP_OK) return s;

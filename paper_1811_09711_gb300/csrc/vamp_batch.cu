@@ -251,7 +251,7 @@ vamp_status vamp_batch_create(const vamp_config* cfgs, int32_t n, int32_t autotu
     for (int i = 0; i < n; ++i) {
         std::string why;
         Params p{};
-        if (!vamp::build_setup(&cfgs[i], p, setups[i], why)) {
+        if (cfgs[i].stratified || !vamp::build_setup(&cfgs[i], p, setups[i], why)) {  // batches: importance sampling
             delete b;
             return VAMP_ERR_INVALID_ARG;
         }

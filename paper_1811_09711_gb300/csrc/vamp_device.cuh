@@ -134,6 +134,13 @@ struct Params {
     double* Vc;        // [K]
     double* Wc;        // [K]
     Scalars* sc;
+    // pseudo-stratified sampling (§3.3), when stratified != 0
+    int stratified;
+    int64_t* nr;       // [K] cells per r axis
+    int64_t* spc;      // [K] calls per cell
+    int64_t* coff;     // [K+1] first cell of each channel
+    double* Qc;        // [K] Σ over the channel's cells of (Σ_cell (w - s_c))^2
+    double* cellsum;   // [Σ cells] Σ_cell (w - s_c) of the pass (context-owned, grows)
 };
 
 // ---------------------------------------------------------------------------
@@ -188,6 +195,12 @@ template <> struct Prec<double> {
     static __device__ __forceinline__ double gk2(const Params& P) { return P.gk2; }
     // in-bin fraction of the forward map: the exact 33-bit value
     static __device__ __forceinline__ double frac(uint64_t low33) { return (double)low33 * 0x1p-33; }
+    // in-bin fraction of a stratified call: remainder over n_r 2^33, one
+    // correctly rounded division
+    static __device__ __forceinline__ double frac_div(uint64_t rem, uint64_t den)
+    {
+        return __ddiv_rn((double)rem, (double)den);
+    }
     // x = ξ_j + frac (ξ_{j+1} - ξ_j), rounded as two separate operations
     static __device__ __forceinline__ double lerp(double e0, double e1, double fr)
     {
@@ -229,6 +242,10 @@ template <> struct Prec<float> {
     static __device__ __forceinline__ float gk2(const Params& P) { return P.gk2_f; }
     // top 24 bits of the 33-bit fraction (exact conversion)
     static __device__ __forceinline__ float frac(uint64_t low33) { return (float)(uint32_t)(low33 >> 9) * 0x1p-24f; }
+    static __device__ __forceinline__ float frac_div(uint64_t rem, uint64_t den)
+    {
+        return (float)__ddiv_rn((double)rem, (double)den);
+    }
     static __device__ __forceinline__ float lerp(float e0, float e1, float fr) { return fmaf(fr, e1 - e0, e0); }
     static __device__ __forceinline__ float tan_(float v) { return tanf(v); }
     static __device__ __forceinline__ float atan_(float v) { return atanf(v); }
@@ -287,6 +304,9 @@ struct Shape {
     static constexpr int DM = kD ? D_ : DMAX_;  // unrolled loop bound
     static constexpr int DLO = kD ? D_ : DLO_;  // rows below this always exist
     static constexpr int NBC = NB_;              // compile-time bins (0: runtime)
+    // pseudo-stratified passes run only in the fully generic shape (the
+    // specialised kernels are compiled without that code)
+    static constexpr bool kStrat = !kD && !kN && DMAX_ == DMAX && DLO_ == 1;
     static constexpr BlkLayout C = make_layout_c<T>(kD ? D_ : 1, kN ? NB_ : 1);
     const BlkLayout L;
     const int d_rt, n_rt;
@@ -345,7 +365,7 @@ __device__ __forceinline__ int lookup(const SH& sh, const unsigned char* row, in
 template <typename T, class SH>
 __device__ __forceinline__ void forward_call(const Params& P, const SH& sh, int c, const uint32_t* X,
                                              T (&x)[SH::DM], T (&p)[SH::DM], int (&jf)[SH::DM], T& own_gJ,
-                                             T& asum_all)
+                                             T& asum_all, const uint32_t* dig = nullptr, uint32_t nr = 1u)
 {
     const int d = sh.d(), n = sh.n();
     const unsigned char* blk = Prec<T>::lk(P) + (size_t)c * sh.bytes();
@@ -353,9 +373,21 @@ __device__ __forceinline__ void forward_call(const Params& P, const SH& sh, int 
 #pragma unroll
     for (int k = 0; k < SH::DM; ++k) {
         if (sh.has(k)) {
-            const uint64_t t = (2ull * X[k] + 1ull) * (uint64_t)n;
-            const int j = (int)(t >> 33);
-            const T fr = Prec<T>::frac(t & ((1ull << 33) - 1ull));
+            int j;
+            T fr;
+            if (dig) {
+                // stratified call: r_k = (a_k + u_k) / n_r, from the integer
+                // (2^33 a_k + 2X + 1) n over n_r 2^33 (n_r = 1: the line below)
+                const uint64_t den = (uint64_t)nr << 33;
+                const uint64_t t = (((uint64_t)dig[k] << 33) + 2ull * X[k] + 1ull) * (uint64_t)n;
+                const uint64_t jj = t / den;
+                j = (int)jj;
+                fr = Prec<T>::frac_div(t - jj * den, den);
+            } else {
+                const uint64_t t = (2ull * X[k] + 1ull) * (uint64_t)n;
+                j = (int)(t >> 33);
+                fr = Prec<T>::frac(t & ((1ull << 33) - 1ull));
+            }
             const unsigned char* row = sh.row(blk, k);
             const T* e = reinterpret_cast<const T*>(row);
             x[k] = Prec<T>::lerp(__ldg(e + j), __ldg(e + j + 1), fr);

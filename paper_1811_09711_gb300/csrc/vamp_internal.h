@@ -78,6 +78,7 @@ bool build_setup(const vamp_config* cfg, Params& P, Setup& S, std::string& why);
 // Device-side placement of the per-problem arrays inside one buffer.
 struct Arena {
     size_t edges64, lk64, lk32, alpha, alpha32, shift, acum, nc, pc, D, csum, ic, vc, wc, pk64, pk32, sc;
+    size_t nr, spc, coff, qc;
     size_t bytes;
 };
 Arena plan_arena(const Params& P);
@@ -89,8 +90,9 @@ cudaError_t upload_setup(const Params& P, const Setup& S, cudaStream_t s);
 // (TILE_BUDGET), or `minb` CTAs per SM of the current device.
 void pass_smem(const Params& P, int fp32, int* tile, size_t* smem_int, size_t* smem_gen);
 void pass_smem_for(const Params& P, int fp32, int minb, int* tile, size_t* smem_int, size_t* smem_gen);
-// Candidate kernels for a shape: exact (D, NB) matches first, then generic.
-std::vector<const PassVariant*> pass_candidates(int fp32, int d, int n);
+// Candidate kernels for a shape: exact (D, NB) matches first, then generic
+// (generic only for pseudo-stratified problems).
+std::vector<const PassVariant*> pass_candidates(int fp32, int d, int n, int stratified = 0);
 // Raises (never lowers) the dynamic shared-memory limit of a kernel.
 cudaError_t ensure_smem(const void* fn, size_t bytes);
 
@@ -134,6 +136,7 @@ const void* pass_multi_kernel(int fp32, int minb);
 
 cudaError_t launch_begin_pass(const Params& P, int64_t N, cudaStream_t s);
 cudaError_t launch_finish_pass(const Params& P, int combine, cudaStream_t s);
+cudaError_t launch_strat_q(const Params& P, cudaStream_t s);  // stratified passes, before finish
 cudaError_t launch_derive(const Params& P, cudaStream_t s);
 cudaError_t launch_refine(const Params& P, cudaStream_t s);
 cudaError_t launch_update_alpha(const Params& P, cudaStream_t s);

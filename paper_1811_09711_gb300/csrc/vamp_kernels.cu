@@ -15,16 +15,48 @@ namespace vamp {
 // ---------------------------------------------------------------------------
 // allocation (R6: N_c = max(N_min, floor(α_c N)) for α_c > 0)
 // ---------------------------------------------------------------------------
+// Pseudo-stratified sampling (§3.3): the largest m in [1, 2^20] with
+// 2 m^d <= N (exact integer search).
+__device__ int64_t strat_cells_per_axis(int64_t N, int d)
+{
+    int64_t lo = 1, hi = 1 << 20;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) / 2;
+        int64_t prod = 2;
+        for (int k = 0; k < d && prod <= N; ++k) {
+            if (prod > N / mid) { prod = N + 1; break; }
+            prod *= mid;
+        }
+        if (prod <= N) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
 __device__ void begin_pass_dev(const Params& P, int64_t N)
 {
     {
-        int64_t acc = 0;
+        int64_t acc = 0, cells = 0;
         P.Pc[0] = 0;
+        if (P.stratified) P.coff[0] = 0;
         for (int c = 0; c < P.K; ++c) {
             int64_t nc = 0;
             if (P.alpha[c] > 0.0) {
                 nc = (int64_t)floor(P.alpha[c] * (double)N);
                 if (nc < P.n_min) nc = P.n_min;
+            }
+            if (P.stratified) {
+                // whole cells: n_r per axis, C = n_r^d cells, s = floor(N_c / C)
+                int64_t m = 1, C = 1, s = nc;
+                if (nc >= 2) {
+                    m = strat_cells_per_axis(nc, P.d);
+                    for (int k = 0; k < P.d; ++k) C *= m;
+                    s = nc / C;
+                }
+                nc = s * C;
+                P.nr[c] = m;
+                P.spc[c] = s;
+                cells += C;
+                P.coff[c + 1] = cells;
             }
             P.Nc[c] = nc;
             acc += nc;
@@ -33,6 +65,27 @@ __device__ void begin_pass_dev(const Params& P, int64_t N)
         P.sc->n_total = acc;
         P.sc->wmax_bits = 0ull;
     }
+}
+
+// Stratified passes: Q_c = Σ over the channel's cells of the squared cell
+// sums, one block per channel, fixed-order reduction.
+__global__ void k_strat_q(Params P)
+{
+    __shared__ double part[256];
+    const int c = blockIdx.x;
+    const int64_t a = P.coff[c], b = P.coff[c + 1];
+    double s = 0.0;
+    for (int64_t q = a + threadIdx.x; q < b; q += blockDim.x) {
+        const double v = P.cellsum[q];
+        s += v * v;
+    }
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) part[threadIdx.x] += part[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) P.Qc[c] = part[0];
 }
 
 __global__ void k_begin_pass(Params P, int64_t N)
@@ -54,7 +107,13 @@ __device__ void finish_pass_dev(const Params& P, int combine)
         const double m1 = P.csum[2 * c] / Nc, m2 = P.csum[2 * c + 1] / Nc;
         const double Ic = P.shift[c] + m1;
         double Vv = 0.0;
-        if (nci > 1) Vv = (m2 - m1 * m1) * Nc / (Nc - 1.0);
+        if (!P.stratified) {
+            if (nci > 1) Vv = (m2 - m1 * m1) * Nc / (Nc - 1.0);
+        } else if (P.spc[c] >= 2) {
+            // mean over the channel's cells of the cells' sample variances
+            const double s = (double)P.spc[c], C = (double)(P.coff[c + 1] - P.coff[c]);
+            Vv = (P.csum[2 * c + 1] - P.Qc[c] / s) / (C * (s - 1.0));
+        }
         if (Vv < 0.0) Vv = 0.0;
         P.Ic[c] = Ic;
         P.Vc[c] = Vv;
@@ -406,7 +465,18 @@ __global__ void k_eval(Params P, EvalArgs A)
     bool skip[1];
     int jf[DMAX];
     T owngJ;
-    forward_call<T>(P, sh, c, X, x, p1[0], jf, owngJ, Aq[0]);
+    if (A.mode == 0 && P.stratified) {
+        const uint32_t nr = (uint32_t)P.nr[c];
+        uint32_t cell = (uint32_t)(((int64_t)call - P.Pc[c]) / P.spc[c]);
+        uint32_t dig[DMAX];
+        for (int k = 0; k < DMAX; ++k) {
+            dig[k] = cell % nr;
+            cell /= nr;
+        }
+        forward_call<T>(P, sh, c, X, x, p1[0], jf, owngJ, Aq[0], dig, nr);
+    } else {
+        forward_call<T>(P, sh, c, X, x, p1[0], jf, owngJ, Aq[0]);
+    }
     g[0] = Prec<T>::alpha(P, c) * owngJ;
     f[0] = P.matching ? T(0) : integrand_peaks<T, DMAX>(P, d, p1[0], Aq[0]);
     int* bins = A.bins + (size_t)q * P.K * d;
@@ -574,6 +644,12 @@ cudaError_t launch_wait_selftest(long long limit, unsigned int* flag, long long*
 cudaError_t launch_begin_pass(const Params& P, int64_t N, cudaStream_t s)
 {
     k_begin_pass<<<1, 32, 0, s>>>(P, N);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_strat_q(const Params& P, cudaStream_t s)
+{
+    k_strat_q<<<P.K, 256, 0, s>>>(P);
     return cudaGetLastError();
 }
 

@@ -78,6 +78,10 @@ extern "C" vamp_status vamp_sample_pass_static(const vamp_config* cfg, const dou
     Params pr{};
     vamp::Setup S;
     std::string why;
+    if (cfg->stratified) {
+        put_msg(err_msg, err_len, "the allocation-free pass samples by importance only (stratified = 0)");
+        return VAMP_ERR_INVALID_ARG;
+    }
     if (!vamp::build_setup(cfg, pr, S, why)) {
         put_msg(err_msg, err_len, ("invalid problem description: " + why).c_str());
         return VAMP_ERR_INVALID_ARG;

@@ -56,6 +56,15 @@ struct Calls {
     uint32_t xacc[CPT];
 };
 
+// Cell sums of a stratified batch: the call at local index l (from the
+// channel's first call) belongs to cell coff + l / spc.
+struct CellSums {
+    double* sum;     // nullptr: importance sampling
+    int64_t l0;      // local index of the batch's first call
+    int64_t spc;     // calls per cell
+    int64_t coff;    // first cell of the channel
+};
+
 // Phase A: Philox words, channel, forward map on the channel's grid, own
 // term of g(p), Gaussian exponent sum; the integrand when peaks are not the
 // channels' maps.  Call q of this thread is base + q*PASS_THREADS + tid.
@@ -90,7 +99,20 @@ __device__ __forceinline__ void phase_a(const Params& P, const SH& sh, uint32_t 
         T x[DM];
         int jf[DM];
         T owngJ, Aq;
-        forward_call<T>(P, sh, c, X, x, C.p[q], jf, owngJ, Aq);
+        if (MODE == 0 && SH::kStrat && P.stratified) {
+            // cell of the call and its base-n_r digits (§3.3)
+            const uint32_t nr = (uint32_t)P.nr[c];
+            uint32_t cell = (uint32_t)(((C.valid[q] ? i : base) - P.Pc[c]) / P.spc[c]);
+            uint32_t dig[DM];
+#pragma unroll
+            for (int k = 0; k < DM; ++k) {
+                dig[k] = cell % nr;
+                cell /= nr;
+            }
+            forward_call<T>(P, sh, c, X, x, C.p[q], jf, owngJ, Aq, dig, nr);
+        } else {
+            forward_call<T>(P, sh, c, X, x, C.p[q], jf, owngJ, Aq);
+        }
         C.Aexp[q] = Aq;
 #pragma unroll
         for (int w = 0; w < (DM + 3) / 4; ++w) {
@@ -142,7 +164,8 @@ __device__ __forceinline__ uint32_t pick(const uint32_t (&a)[W], int i)
 // different rows.
 template <typename T, int CPT, class SH>
 __device__ __forceinline__ void phase_c_int(const SH& sh, const Calls<T, CPT, SH::DM>& C, double sft, double* Ds,
-                                            double& s1, double& s2, double& wm, bool& bad)
+                                            double& s1, double& s2, double& wm, bool& bad,
+                                            const CellSums cs = CellSums{nullptr, 0, 1, 0})
 {
     constexpr int DM = SH::DM;
     const int d = sh.d(), n = sh.n();
@@ -156,6 +179,8 @@ __device__ __forceinline__ void phase_c_int(const SH& sh, const Calls<T, CPT, SH
         const double dv = w - sft;
         s1 += dv;
         s2 += dv * dv;
+        if (cs.sum)  // stratified: the sum of the call's cell
+            atomicAdd(&cs.sum[cs.coff + (cs.l0 + q * PASS_THREADS + (int)threadIdx.x) / cs.spc], dv);
         wm = fmax(wm, w);
         const double w2 = w * w;
 #pragma unroll
@@ -327,7 +352,10 @@ __global__ void __launch_bounds__(PASS_THREADS, MINB) k_pass(Params P, PassArgs 
 
         // ---- phase C: weights and accumulation ------------------------------
         if (MODE == 0) {
-            phase_c_int<T, CPT>(sh, C, sft, Ds, s1, s2, wm, bad);
+            phase_c_int<T, CPT>(sh, C, sft, Ds, s1, s2, wm, bad,
+                                (SH::kStrat && P.stratified)
+                                    ? CellSums{P.cellsum, base - P.Pc[cseg], P.spc[cseg], P.coff[cseg]}
+                                    : CellSums{nullptr, 0, 1, 0});
             i0 = end;
             if (i0 >= seg_end) {
                 // end of the segment: flush its sums and d-values

@@ -615,7 +615,7 @@ vamp_status vamp_server_submit(vamp_server* s, const vamp_config* cfg, int32_t i
     r->cfg.peaks = r->pk.data();
     r->cfg.peak_weight = r->w.data();
     std::string why;
-    if (!vamp::build_setup(&r->cfg, r->P, r->S, why)) {
+    if (cfg->stratified || !vamp::build_setup(&r->cfg, r->P, r->S, why)) {  // requests: importance sampling
         delete r;
         return VAMP_ERR_INVALID_ARG;
     }

@@ -131,6 +131,7 @@ bool build_setup(const vamp_config* cfg, Params& pr, Setup& S, std::string& why)
     if (cfg->n_min < 1) { why = "n_min must be >= 1"; return false; }
     if (cfg->gen_batch < 0 || cfg->gen_batch > (int64_t(1) << 24)) { why = "gen_batch out of range"; return false; }
     if (cfg->precision != VAMP_PREC_FP64 && cfg->precision != VAMP_PREC_FP32_EVAL) { why = "bad precision"; return false; }
+    if (cfg->stratified != 0 && cfg->stratified != 1) { why = "stratified must be 0 or 1"; return false; }
     for (int q = 0; q < P; ++q)
         if (!std::isfinite(cfg->peak_weight[q])) { why = "peak weights must be finite"; return false; }
 
@@ -145,6 +146,7 @@ bool build_setup(const vamp_config* cfg, Params& pr, Setup& S, std::string& why)
     pr.beta = cfg->beta;
     pr.smooth = cfg->smooth;
     pr.omega_mode = cfg->omega_mode;
+    pr.stratified = cfg->stratified;
     // Gaussian factor exp(-(p-c)²/(2σ²)) / Z written as 2^-((p-c)² gk2) / Z,
     // gk2 = log2(e) / (2σ²); σ = 0 switches it off (factor 1)
     S.zinv = 1.0;
@@ -208,6 +210,10 @@ Arena plan_arena(const Params& P)
     A.pk64 = take((size_t)P.P * sizeof(MapRec<double>));
     A.pk32 = take((size_t)P.P * sizeof(MapRec<float>));
     A.sc = take(sizeof(Scalars));
+    A.nr = take(K * 8);
+    A.spc = take(K * 8);
+    A.coff = take((K + 1) * 8);
+    A.qc = take(K * 8);
     A.bytes = off;
     return A;
 }
@@ -231,6 +237,11 @@ void bind_arena(Params& P, unsigned char* b, const Arena& A)
     P.pk64 = (const MapRec<double>*)(b + A.pk64);
     P.pk32 = (const MapRec<float>*)(b + A.pk32);
     P.sc = (Scalars*)(b + A.sc);
+    P.nr = (int64_t*)(b + A.nr);
+    P.spc = (int64_t*)(b + A.spc);
+    P.coff = (int64_t*)(b + A.coff);
+    P.Qc = (double*)(b + A.qc);
+    P.cellsum = nullptr;  // sized per pass by the context
 }
 
 cudaError_t upload_setup(const Params& P, const Setup& S, cudaStream_t s)
@@ -278,7 +289,7 @@ void pass_smem_for(const Params& P, int fp32, int minb, int* tile, size_t* smem_
     smem_for_budget(P, fp32, budget, tile, smem_int, smem_gen);
 }
 
-std::vector<const PassVariant*> pass_candidates(int fp32, int d, int n)
+std::vector<const PassVariant*> pass_candidates(int fp32, int d, int n, int stratified)
 {
     static std::vector<PassVariant> all;
     static std::once_flag once;
@@ -290,7 +301,7 @@ std::vector<const PassVariant*> pass_candidates(int fp32, int d, int n)
     std::vector<const PassVariant*> exact, generic;
     for (const PassVariant& v : all) {
         if (v.fp32 != fp32) continue;
-        if (v.D == d && v.NB == n) exact.push_back(&v);
+        if (v.D == d && v.NB == n && !stratified) exact.push_back(&v);
         else if (v.D == 0 && v.NB == 0) generic.push_back(&v);
     }
     for (const PassVariant* v : generic) exact.push_back(v);

@@ -52,6 +52,7 @@ class Config(C.Structure):
         ("grid_alpha", C.c_double), ("beta", C.c_double), ("n_min", C.c_int64),
         ("smooth", C.c_int32), ("omega_mode", C.c_int32),
         ("gen_batch", C.c_int64), ("combine_from", C.c_int32), ("precision", C.c_int32),
+        ("stratified", C.c_int32),
     ]
 
 
@@ -192,7 +193,7 @@ def make_config(problem, precision: int = PREC_FP64):
                  int(problem.seed) & (2**64 - 1), int(problem.request_id) & 0xffffffff,
                  float(problem.grid_alpha), float(problem.beta), int(problem.n_min),
                  int(problem.smooth), int(problem.omega_mode), int(problem.gen_batch),
-                 int(problem.combine_from), int(precision))
+                 int(problem.combine_from), int(precision), int(getattr(problem, "stratified", 0)))
     return cfg, (ch, pk, w)
 
 

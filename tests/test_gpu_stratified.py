@@ -1,0 +1,91 @@
+"""Pseudo-stratified sampling in r space (§3.3) on the GPU against the FP64
+oracle: the cells, forward bins and per-call values bit-exact / 1e-12,
+whole adaptation runs (integral, stratified variance, D, edges, α) within
+1e-12 in FP64, the FP32-eval form within its tolerance; batches, servers and
+the allocation-free pass reject the mode."""
+import numpy as np
+import pytest
+
+from paper_1811_09711_gb300 import problems as P
+from test_gpu_parity import NTHREADS, rel, run_schedule
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def V():
+    from paper_1811_09711_gb300 import vamp
+    return vamp
+
+
+@pytest.fixture(scope="module")
+def O(oracle_mod):
+    return oracle_mod
+
+
+@pytest.mark.parametrize("factory,calls", [(P.single_gauss, 60_000), (P.bw_gauss, 300_000)])
+def test_stratified_schedule_fp64(V, O, factory, calls):
+    pr = factory().replace(stratified=1, combine_from=1)
+    o = O.Oracle(pr)
+    N = o.allocate(calls)
+    assert N < calls  # whole cells: the remainder is not sampled
+    run_schedule(V, O, pr, 3, calls)
+
+
+def test_stratified_calls_bit_exact_fp64(V, O):
+    pr = P.bw_gauss().replace(stratified=1)
+    o = O.Oracle(pr)
+    g = V.Vamp(pr)
+    for it in range(2):
+        o.sample_pass(200_000, it, n_threads=NTHREADS)
+        o.refine_grids()
+        o.update_alpha()
+    st = o.get_state()
+    g.set_state(st["edges"], st["alpha"], st["shift"], st["w_max"])
+    N = 500_000
+    assert g.allocate(N) == o.allocate(N)
+    n_tot = o.allocate(N)
+    for c0 in list(range(0, 400, 50)) + list(np.linspace(0, n_tot - 50, 8).astype(int)):
+        r = g.eval_calls(0, 7, int(c0), 50)
+        for q in range(50):
+            ref = o.eval_call(0, 7, int(c0) + q)
+            assert r["channel"][q] == ref["channel"]
+            assert np.array_equal(r["jf"][q], ref["jf"]), int(c0) + q
+            assert np.array_equal(r["bins"][q], ref["bins"])
+            assert rel(r["x"][q], ref["x"]) < 1e-13
+            assert rel(r["w"][q], ref["w"]) < 1e-12
+
+
+def test_stratified_fp32_eval_accuracy(V, O):
+    pr = P.bw_gauss().replace(stratified=1)
+    o = O.Oracle(pr)
+    g = V.Vamp(pr, precision=1)
+    for it in range(2):
+        o.sample_pass(300_000, it, n_threads=NTHREADS)
+        o.refine_grids()
+        o.update_alpha()
+    st = o.get_state()
+    g.set_state(st["edges"], st["alpha"], st["shift"], st["w_max"])
+    rg = g.sample_pass(1_000_000, 2)
+    ro = o.sample_pass(1_000_000, 2, n_threads=NTHREADS)
+    assert rg.n_calls == ro.n_calls
+    assert rel(rg.integral, ro.integral) < 1e-6
+    assert abs(rg.integral - ro.integral) < 0.05 * np.sqrt(ro.variance)
+    assert rel(rg.variance, ro.variance) < 1e-3
+
+
+def test_batch_server_and_static_reject_stratified(V):
+    import torch
+    pr = P.bw_gauss().replace(stratified=1)
+    with pytest.raises(V.VampError):
+        V.Batch([pr], precision=1)
+    srv = V.Server(max_slots=2, precision=1)
+    with pytest.raises(V.VampError):
+        srv.submit(pr, 2, 10_000)
+    srv.close()
+    st = V.Vamp(pr.replace(stratified=0)).get_state()
+    e = torch.tensor(st["edges"], dtype=torch.float64, device="cuda")
+    a = torch.tensor(st["alpha"], dtype=torch.float64, device="cuda")
+    s = torch.tensor(st["shift"], dtype=torch.float64, device="cuda")
+    with pytest.raises(V.VampError):
+        V.sample_pass_static(pr, 1, e.data_ptr(), a.data_ptr(), s.data_ptr(), 10_000, 0)

@@ -57,7 +57,7 @@ MUTATIONS = [
      "philox_known_answers"),
     ("counter_fields_swapped", "uint32_t ctr[4] = { call, (uint32_t)b, field, o->request }, out[4];",
      "uint32_t ctr[4] = { call, field, (uint32_t)b, o->request }, out[4];", "call_words_layout"),
-    ("forward_bin_shift", "int j = (int)(t >> 33);", "int j = (int)(t >> 34);",
+    ("forward_bin_shift", "j = (int)(t >> 33);", "j = (int)(t >> 34);",
      "forward_map_uniform_grid"),
     ("channel_choice_reflected", "double tgt = u * A[o->K - 1];",
      "double tgt = (1.0 - u) * A[o->K - 1];", "channel_choice_is_inverse_cdf"),
