@@ -57,6 +57,7 @@ class _Problem(C.Structure):
         ("smooth", C.c_int32), ("omega_mode", C.c_int32),
         ("gen_batch", C.c_int64),
         ("stratified", C.c_int32),
+        ("n_equiv", C.c_int32), ("equiv", C.c_void_p),
     ]
 
 
@@ -108,6 +109,8 @@ def _load():
             lib.or_allocate_raw.restype = i64
             lib.or_strat_cells_per_axis.argtypes = [i64, C.c_int]
             lib.or_strat_cells_per_axis.restype = i64
+            lib.or_get_pooled.argtypes = [vp, vp]
+            lib.or_get_pooled.restype = C.c_int
             _lib = lib
     return _lib
 
@@ -198,6 +201,9 @@ class Oracle:
             np.ascontiguousarray(pk.kind, np.int32), np.ascontiguousarray(pk.a, np.float64),
             np.ascontiguousarray(pk.b, np.float64),
         ]
+        eq = getattr(pr, "equivalences", None)
+        eq = np.zeros((0, 2 + 2 * self.d), np.int32) if eq is None else np.ascontiguousarray(eq, np.int32)
+        self._keep.append(eq)
         k = self._keep
         st = _Problem(self.d, self.K, self.n, _ptr(k[0]).value, _ptr(k[1]).value, _ptr(k[2]).value,
                       _ptr(k[3]).value, _ptr(k[4]).value, self.P, _ptr(k[5]).value,
@@ -205,7 +211,8 @@ class Oracle:
                       _ptr(k[10]).value, float(pr.gauss_sigma), float(pr.gauss_centre),
                       int(pr.gauss_norm), int(pr.seed) & (2**64 - 1), int(pr.request_id),
                       float(pr.grid_alpha), float(pr.beta), int(pr.n_min), int(pr.smooth),
-                      int(pr.omega_mode), int(pr.gen_batch), int(getattr(pr, "stratified", 0)))
+                      int(pr.omega_mode), int(pr.gen_batch), int(getattr(pr, "stratified", 0)),
+                      int(eq.shape[0]), _ptr(eq).value if eq.shape[0] else None)
         status = C.c_int(0)
         self.h = self.lib.or_create(C.byref(st), C.byref(status))
         if not self.h:
@@ -281,6 +288,14 @@ class Oracle:
         Nc = np.zeros(self.K, np.int64)
         self.lib.or_get_pass(self.h, _ptr(D), _ptr(Ic), _ptr(Vc), _ptr(Nc))
         return {"D": D, "Ic": Ic, "Vc": Vc, "Nc": Nc}
+
+    def get_pooled(self):
+        """Bin weights the next refinement uses (after the equivalences, R18)."""
+        D = np.zeros((self.K, self.d, self.n), np.float64)
+        rc = self.lib.or_get_pooled(self.h, _ptr(D))
+        if rc != OR_OK:
+            raise RuntimeError(f"oracle get_pooled failed ({rc})")
+        return D
 
     # -- point functions -----------------------------------------------------
     def f(self, p) -> float:

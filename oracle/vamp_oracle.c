@@ -55,6 +55,15 @@
  *       α update is the mean over the channel's cells of the cells' sample
  *       variances, [Σ d² - Σ_cells (Σ_cell d)² / s] / (C (s - 1)) with
  *       d = w - s_c (R13); 0 for s < 2.
+ *   R18 channel equivalences (§3.5, optional): the bin weights that the
+ *       rebinning of channel c uses are its d-values D_c (R1) plus, for each
+ *       listed equivalence (c <- c', π, mode per axis), the d-values of axis
+ *       π(k) of c': identity adds D_{c',π(k),j}; invert adds D_{c',π(k),n-1-j}
+ *       (the paper's "d - j" read as the mirrored bin of an n-bin axis);
+ *       symmetric adds the mean of the two; invariant sets the row to 1 (the
+ *       rebinning then keeps the axis).  All sums read the pass's own D (the
+ *       equivalences act at once, not one after another), terms add in list
+ *       order, and c' = c is allowed.
  */
 #include <float.h>
 #include <math.h>
@@ -68,6 +77,7 @@
 #define OR_MAX_D 64
 
 enum { OR_MAP_ID = 0, OR_MAP_BW = 1, OR_MAP_POW = 2 };
+enum { OR_EQ_IDENTITY = 0, OR_EQ_INVERT = 1, OR_EQ_SYMMETRIC = 2, OR_EQ_INVARIANT = 3 };
 enum { OR_OK = 0, OR_ERR_ARG = 1, OR_ERR_STATE = 2, OR_ERR_NUMERIC = 3, OR_ERR_MEM = 4 };
 
 /* Problem as handed over by the harness (arrays are copied). */
@@ -88,6 +98,8 @@ typedef struct {
     int32_t smooth, omega_mode;
     int64_t gen_batch;
     int32_t stratified;                          /* R16 */
+    int32_t n_equiv;                             /* R18 */
+    const int32_t *equiv;                        /* n_equiv records: c, c', π[d], mode[d] */
 } or_problem;
 
 /* Neumaier-compensated sum. */
@@ -131,6 +143,9 @@ typedef struct or_ctx {
     int64_t *nr, *spc, *Cc; /* K each: cells per axis, points per cell, cells */
     int64_t n_total;
     double *D;       /* K*d*n */
+    int n_eq;        /* R18 */
+    int32_t *eq;     /* n_eq * (2 + 2d) */
+    double *Dp;      /* K*d*n: bin weights after the equivalences */
     double *Ic, *Vc, *Wc; /* K */
     int have_pass;
     double wmax;
@@ -413,6 +428,7 @@ void or_destroy(or_ctx *o)
     free(o->ch); free(o->pk); free(o->pk_w); free(o->edges); free(o->alpha); free(o->shift);
     free(o->Nc); free(o->Pc); free(o->D); free(o->Ic); free(o->Vc); free(o->Wc);
     free(o->nr); free(o->spc); free(o->Cc);
+    free(o->eq); free(o->Dp);
     free(o);
 }
 
@@ -445,6 +461,24 @@ or_ctx *or_create(const or_problem *pr, int *status)
         or_destroy(o); *status = OR_ERR_MEM; return NULL;
     }
     o->stratified = pr->stratified ? 1 : 0;
+    if (pr->n_equiv < 0 || (pr->n_equiv > 0 && !pr->equiv)) { or_destroy(o); return NULL; }
+    if (pr->n_equiv > 0) {
+        const int rl = 2 + 2 * o->d;
+        o->n_eq = pr->n_equiv;
+        o->eq = malloc((size_t)o->n_eq * rl * sizeof(int32_t));
+        o->Dp = calloc(nd, sizeof(double));
+        if (!o->eq || !o->Dp) { or_destroy(o); *status = OR_ERR_MEM; return NULL; }
+        memcpy(o->eq, pr->equiv, (size_t)o->n_eq * rl * sizeof(int32_t));
+        for (int e = 0; e < o->n_eq; ++e) {
+            const int32_t *r = o->eq + (size_t)e * rl;
+            int bad = r[0] < 0 || r[0] >= o->K || r[1] < 0 || r[1] >= o->K;
+            for (int k = 0; k < o->d && !bad; ++k) {
+                bad = r[2 + k] < 0 || r[2 + k] >= o->d || r[2 + o->d + k] < 0 || r[2 + o->d + k] > 3;
+                for (int q = 0; q < k && !bad; ++q) bad = r[2 + q] == r[2 + k]; /* π a permutation */
+            }
+            if (bad) { or_destroy(o); return NULL; }
+        }
+    }
     if (load_maps(o->ch, o->K, o->d, pr->ch_nmap, pr->ch_coord, pr->ch_kind, pr->ch_a, pr->ch_b) ||
         load_maps(o->pk, o->P, o->d, pr->pk_nmap, pr->pk_coord, pr->pk_kind, pr->pk_a, pr->pk_b)) {
         or_destroy(o); return NULL;
@@ -783,13 +817,53 @@ static void refine_row(const double *Din, int n, int smooth, double alpha_grid, 
     free(Dj); free(m); free(C); free(ne);
 }
 
+/* R18: bin weights of every channel after the channel equivalences. */
+static void pool_equivalences(or_ctx *o)
+{
+    const int d = o->d, n = o->n, rl = 2 + 2 * d;
+    for (int c = 0; c < o->K; ++c)
+        for (int k = 0; k < d; ++k) {
+            double *out = o->Dp + ((size_t)c * d + k) * n;
+            const double *own = o->D + ((size_t)c * d + k) * n;
+            int invariant = 0;
+            for (int j = 0; j < n; ++j) out[j] = own[j];
+            for (int e = 0; e < o->n_eq; ++e) {
+                const int32_t *r = o->eq + (size_t)e * rl;
+                if (r[0] != c) continue;
+                const int mode = r[2 + d + k];
+                const double *src = o->D + ((size_t)r[1] * d + r[2 + k]) * n;
+                for (int j = 0; j < n; ++j) {
+                    if (mode == OR_EQ_IDENTITY) out[j] += src[j];
+                    else if (mode == OR_EQ_INVERT) out[j] += src[n - 1 - j];
+                    else if (mode == OR_EQ_SYMMETRIC) out[j] += 0.5 * (src[j] + src[n - 1 - j]);
+                }
+                if (mode == OR_EQ_INVARIANT) invariant = 1;
+            }
+            if (invariant)
+                for (int j = 0; j < n; ++j) out[j] = 1.0;
+        }
+}
+
 int or_refine_grids(or_ctx *o)
 {
     if (!o->have_pass) return OR_ERR_STATE;
+    const double *W = o->D;
+    if (o->n_eq > 0) { pool_equivalences(o); W = o->Dp; }
     for (int c = 0; c < o->K; ++c)
         for (int k = 0; k < o->d; ++k)
-            refine_row(o->D + ((size_t)c * o->d + k) * o->n, o->n, o->smooth, o->grid_alpha,
+            refine_row(W + ((size_t)c * o->d + k) * o->n, o->n, o->smooth, o->grid_alpha,
                        edge_row(o, c, k));
+    return OR_OK;
+}
+
+/* The bin weights the next refinement would use (R18; D itself without
+ * equivalences). */
+int or_get_pooled(or_ctx *o, double *out)
+{
+    if (!o->have_pass) return OR_ERR_STATE;
+    const size_t nd = (size_t)o->K * o->d * o->n;
+    if (o->n_eq > 0) { pool_equivalences(o); memcpy(out, o->Dp, nd * sizeof(double)); }
+    else memcpy(out, o->D, nd * sizeof(double));
     return OR_OK;
 }
 

@@ -24,6 +24,9 @@ integrands stand in for them:
   channels log-uniform in 1..64, calls log-uniform in 1e4..1e7, bins in
   {20, 50, 100}), each built like ``bw_gauss``.
 * ``serving_stream``: Poisson arrivals of integrate-then-generate requests.
+* ``ring``: channels that are images of one another under a cyclic shift
+  of coordinates (and mirror-symmetric on every axis), with the channel
+  equivalences that say so (§3.5).
 
 All randomness comes from ``numpy.random.default_rng(seed)`` (PCG64), which
 gives identical streams on x86-64 and AArch64.
@@ -43,6 +46,12 @@ GAUSS_NORM_REAL_LINE = 0  # Gaussian normalised on the whole real line
 GAUSS_NORM_UNIT = 1       # Gaussian normalised on [0, 1]
 
 MAX_MAPPED = 4            # mapped coordinates per channel / peak
+
+# per-axis kinds of a channel equivalence (§3.5)
+EQ_IDENTITY = 0
+EQ_INVERT = 1
+EQ_SYMMETRIC = 2
+EQ_INVARIANT = 3
 
 
 @dataclasses.dataclass
@@ -103,6 +112,10 @@ class Problem:
     combine_from: int = 0     # first iteration entering the combination
     n_events: int = 0
     stratified: int = 0       # 1: pseudo-stratified sampling in r space (§3.3)
+    # channel equivalences (§3.5): int32[n_equiv, 2 + 2d], each row
+    # (c, c', π_0..π_{d-1}, kind_0..kind_{d-1}): axis k of channel c takes
+    # the bin weights of axis π_k of channel c' with kind EQ_*
+    equivalences: np.ndarray | None = None
 
     @property
     def n_channels(self) -> int:
@@ -288,6 +301,46 @@ def special_case(kind: str, d: int = 2, n_bins: int = 10, seed: int = 7,
                    peak_weight=np.ones(1), peaks=pk, gauss_sigma=0.0,
                    gauss_centre=0.5, gauss_norm=GAUSS_NORM_UNIT, seed=seed,
                    iterations=3, calls=5000, adapt_grid=True, adapt_alpha=False)
+
+
+def ring(n_ring: int = 3, d: int = 6, width: float = 3e-3, seed: int = 11,
+         equivalences: bool = True, kind: int = EQ_IDENTITY) -> Problem:
+    """Channels related by symmetry, with their equivalences (§3.5).
+
+    Channel c < n_ring applies a Breit-Wigner map (mass 0.5, common width)
+    to coordinate c; the integrand is the equal-weight sum of the matching
+    peaks times Gaussians (sigma 0.2, centre 0.5) on the other coordinates.
+    A cyclic shift of coordinates 0..n_ring-1 permutes the peaks, and
+    p_k -> 1 - p_k leaves every factor unchanged, so channel c' samples
+    like channel c with its axes shifted by c' - c.  With ``equivalences``
+    every ordered pair (c, c'), c != c', is listed with that permutation
+    and the per-axis kind ``kind``.
+    """
+    ms = MapSet.identity(n_ring)
+    ms.n_mapped[:] = 1
+    ms.coord[:, 0] = np.arange(n_ring)
+    ms.kind[:, 0] = MAP_BW
+    ms.a[:, 0] = 0.5
+    ms.b[:, 0] = width
+    eq = rotation_equivalences(n_ring, d, kind) if equivalences else None
+    return Problem(name=f"ring_d{d}_k{n_ring}", d=d, n_bins=20, channels=ms,
+                   peak_weight=np.full(n_ring, 1.0 / n_ring), peaks=ms.copy(),
+                   gauss_sigma=0.2, gauss_centre=0.5, gauss_norm=GAUSS_NORM_UNIT,
+                   seed=seed, iterations=5, calls=30_000, adapt_grid=True,
+                   adapt_alpha=True, combine_from=2, equivalences=eq)
+
+
+def rotation_equivalences(n_ring: int, d: int, kind: int = EQ_IDENTITY) -> np.ndarray:
+    """Equivalences of ``ring``: axis k < n_ring of channel c matches axis
+    (k + c' - c) mod n_ring of channel c'; the other axes match themselves."""
+    rows = []
+    for c in range(n_ring):
+        for cp in range(n_ring):
+            if cp == c:
+                continue
+            perm = [(k + cp - c) % n_ring if k < n_ring else k for k in range(d)]
+            rows.append([c, cp] + perm + [kind] * d)
+    return np.array(rows, np.int32).reshape(-1, 2 + 2 * d)
 
 
 CONFIGS = {

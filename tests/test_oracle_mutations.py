@@ -75,6 +75,20 @@ MUTATIONS = [
      "unbiased_and_error", "test_oracle_stratified.py"),
     ("strat_fraction_denominator", "fr = (double)(t % den) / (double)den;", "fr = (double)(t % den) / 0x1p33;",
      "points_lie", "test_oracle_stratified.py"),
+    # channel equivalences (R18): pins in test_oracle_equiv.py
+    ("eq_invert_not_mirrored", "else if (mode == OR_EQ_INVERT) out[j] += src[n - 1 - j];",
+     "else if (mode == OR_EQ_INVERT) out[j] += src[j];", "mirror_symmetric", "test_oracle_equiv.py"),
+    ("eq_symmetric_half_dropped", "out[j] += 0.5 * (src[j] + src[n - 1 - j]);",
+     "out[j] += (src[j] + src[n - 1 - j]);", "mean_of_identity", "test_oracle_equiv.py"),
+    ("eq_sequential_in_place", "const double *src = o->D + ((size_t)r[1] * d + r[2 + k]) * n;",
+     "const double *src = o->Dp + ((size_t)r[1] * d + r[2 + k]) * n;", "rotation_images",
+     "test_oracle_equiv.py"),
+    ("eq_permutation_reversed", "const double *src = o->D + ((size_t)r[1] * d + r[2 + k]) * n;",
+     "int kq = 0; while (r[2 + kq] != k) ++kq;\n"
+     "                const double *src = o->D + ((size_t)r[1] * d + kq) * n;", "rotation_images",
+     "test_oracle_equiv.py"),
+    ("eq_invariant_adds_one", "for (int j = 0; j < n; ++j) out[j] = 1.0;",
+     "for (int j = 0; j < n; ++j) out[j] += 1.0;", "invariant_axis", "test_oracle_equiv.py"),
 ]
 
 
