@@ -61,6 +61,15 @@ typedef enum { VAMP_MAP_ID = 0, VAMP_MAP_BW = 1, VAMP_MAP_POW = 2 } vamp_map_kin
 
 typedef enum { VAMP_GAUSS_NORM_REAL_LINE = 0, VAMP_GAUSS_NORM_UNIT = 1 } vamp_gauss_norm;
 
+/* Per-axis kind of a channel equivalence (§3.5): how the bin weights of the
+ * matched axis of the partner channel enter the rebinning of this axis. */
+typedef enum {
+    VAMP_EQ_IDENTITY = 0,   /* bin j adds the partner's bin j */
+    VAMP_EQ_INVERT = 1,     /* bin j adds the partner's bin n-1-j (mirrored axis) */
+    VAMP_EQ_SYMMETRIC = 2,  /* bin j adds the mean of the partner's bins j and n-1-j */
+    VAMP_EQ_INVARIANT = 3   /* the axis takes unit weights: rebinning keeps it */
+} vamp_equiv_kind;
+
 /* One channel map φ_c, or one integrand peak (same shape).  Slot s <
  * n_mapped maps coordinate coord[s]; all other coordinates are identity.
  *   VAMP_MAP_BW : Breit-Wigner, a = mass m, b = width Γ > 0;
@@ -111,6 +120,15 @@ typedef struct {
                                    the per-call variance is the mean of the cells' sample variances.
                                    Generation stays importance sampling.  Contexts only (batches and
                                    servers reject it). */
+    int32_t n_equiv;            /* channel equivalences (§3.5), 0..65536; 0 = none */
+    const int32_t *equiv;       /* [n_equiv][2 + 2d] host, copied at creation: records
+                                   (c, c', π_0..π_{d-1}, kind_0..kind_{d-1}).  Before each
+                                   rebinning, axis k of channel c takes its own d-values plus, per
+                                   record naming c (in table order), axis π_k of channel c' with
+                                   kind_k (vamp_equiv_kind); all records read the pass's own
+                                   d-values.  π must be a permutation of 0..d-1, c' may equal c.
+                                   Contexts, batches and servers; the allocation-free pass, which
+                                   does not rebin, accepts and ignores them. */
 } vamp_config;
 
 /* Result of one sampling pass (§3.1 Eqs. 10-11 per channel, Eq. 23 overall).

@@ -141,6 +141,12 @@ struct Params {
     int64_t* coff;     // [K+1] first cell of each channel
     double* Qc;        // [K] Σ over the channel's cells of (Σ_cell (w - s_c))^2
     double* cellsum;   // [Σ cells] Σ_cell (w - s_c) of the pass (context-owned, grows)
+    // channel equivalences (§3.5): the bin weights that rebin grid row r are
+    // D[r] plus the terms eq_ent[eq_off[r] .. eq_off[r+1]) in list order, each
+    // (source row << 2 | kind); null without equivalences
+    int n_eq_ent;
+    const int32_t* eq_off;   // [K*d + 1]
+    const int32_t* eq_ent;   // [n_eq_ent]
 };
 
 // ---------------------------------------------------------------------------

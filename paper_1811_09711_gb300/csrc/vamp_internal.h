@@ -69,6 +69,7 @@ struct Setup {
     double zinv = 1.0;
     std::vector<unsigned char> hdr64, hdr32;  // K lookup-block headers each
     std::vector<unsigned char> pk64, pk32;    // P MapRec records each (non-matching integrand)
+    std::vector<int32_t> eq_off, eq_ent;      // channel equivalences by grid row (Params::eq_off)
 };
 
 // Validates cfg, fills the scalar fields of P (keys, layouts, Gaussian,
@@ -79,6 +80,7 @@ bool build_setup(const vamp_config* cfg, Params& P, Setup& S, std::string& why);
 struct Arena {
     size_t edges64, lk64, lk32, alpha, alpha32, shift, acum, nc, pc, D, csum, ic, vc, wc, pk64, pk32, sc;
     size_t nr, spc, coff, qc;
+    size_t eqoff, eqent;   // 0 bytes without equivalences
     size_t bytes;
 };
 Arena plan_arena(const Params& P);

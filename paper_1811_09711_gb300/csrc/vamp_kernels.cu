@@ -255,6 +255,27 @@ __device__ void refine_row_dev(const Params& P, int row, int lane, double* ws)
     const double* Din = P.D + (size_t)row * n;
     double* e = P.edges64 + (size_t)row * (n + 1);
     for (int j = lane; j < n; j += 32) Dj[j] = Din[j];
+    if (P.eq_off) {
+        // channel equivalences (§3.5): the pass's d-values of the equivalent
+        // rows, added in list order (identity j, invert n-1-j, symmetric the
+        // mean of both); an invariant axis takes unit weights
+        const int q0 = P.eq_off[row], q1 = P.eq_off[row + 1];
+        bool invariant = false;
+        for (int q = q0; q < q1; ++q) {
+            const int ent = P.eq_ent[q], kind = ent & 3;
+            const double* src = P.D + (size_t)(ent >> 2) * n;
+            if (kind == VAMP_EQ_INVARIANT) { invariant = true; continue; }
+            for (int j = lane; j < n; j += 32) {
+                double t;
+                if (kind == VAMP_EQ_IDENTITY) t = src[j];
+                else if (kind == VAMP_EQ_INVERT) t = src[n - 1 - j];
+                else t = __dmul_rn(0.5, __dadd_rn(src[j], src[n - 1 - j]));
+                Dj[j] = __dadd_rn(Dj[j], t);
+            }
+        }
+        if (invariant)
+            for (int j = lane; j < n; j += 32) Dj[j] = 1.0;
+    }
     for (int j = lane; j <= n; j += 32) eo[j] = e[j];
     __syncwarp();
     if (P.smooth && n >= 2) {

@@ -619,6 +619,8 @@ vamp_status vamp_server_submit(vamp_server* s, const vamp_config* cfg, int32_t i
         delete r;
         return VAMP_ERR_INVALID_ARG;
     }
+    r->cfg.equiv = nullptr;  // copied into the setup; the caller's table may go away
+    r->cfg.n_equiv = 0;
     if (calls + (int64_t)r->P.K * r->P.n_min > int64_t(0xffffffff)) {
         delete r;
         return VAMP_ERR_INVALID_ARG;

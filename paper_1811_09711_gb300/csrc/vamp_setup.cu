@@ -132,6 +132,24 @@ bool build_setup(const vamp_config* cfg, Params& pr, Setup& S, std::string& why)
     if (cfg->gen_batch < 0 || cfg->gen_batch > (int64_t(1) << 24)) { why = "gen_batch out of range"; return false; }
     if (cfg->precision != VAMP_PREC_FP64 && cfg->precision != VAMP_PREC_FP32_EVAL) { why = "bad precision"; return false; }
     if (cfg->stratified != 0 && cfg->stratified != 1) { why = "stratified must be 0 or 1"; return false; }
+    if (cfg->n_equiv < 0 || cfg->n_equiv > 65536 || (cfg->n_equiv > 0 && !cfg->equiv)) {
+        why = "n_equiv must be in 0..65536 with a table"; return false;
+    }
+    if (cfg->n_equiv > 0 && (int64_t)K * d >= (int64_t(1) << 28)) { why = "too many grid rows for equivalences"; return false; }
+    for (int e = 0; e < cfg->n_equiv; ++e) {
+        const int32_t* r = cfg->equiv + (size_t)e * (2 + 2 * d);
+        if (r[0] < 0 || r[0] >= K || r[1] < 0 || r[1] >= K) { why = "equivalence names a channel out of range"; return false; }
+        unsigned seen = 0;
+        for (int k = 0; k < d; ++k) {
+            if (r[2 + k] < 0 || r[2 + k] >= d || (seen >> r[2 + k] & 1u)) {
+                why = "equivalence axes must be a permutation of 0..d-1"; return false;
+            }
+            seen |= 1u << r[2 + k];
+            if (r[2 + d + k] < VAMP_EQ_IDENTITY || r[2 + d + k] > VAMP_EQ_INVARIANT) {
+                why = "equivalence kind must be 0..3"; return false;
+            }
+        }
+    }
     for (int q = 0; q < P; ++q)
         if (!std::isfinite(cfg->peak_weight[q])) { why = "peak weights must be finite"; return false; }
 
@@ -147,6 +165,21 @@ bool build_setup(const vamp_config* cfg, Params& pr, Setup& S, std::string& why)
     pr.smooth = cfg->smooth;
     pr.omega_mode = cfg->omega_mode;
     pr.stratified = cfg->stratified;
+    // equivalences regrouped by target grid row, list order kept (§3.5)
+    S.eq_off.assign(cfg->n_equiv > 0 ? (size_t)K * d + 1 : 0, 0);
+    S.eq_ent.clear();
+    if (cfg->n_equiv > 0) {
+        for (int row = 0; row < K * d; ++row) {
+            const int c = row / d, k = row % d;
+            S.eq_off[row] = (int32_t)S.eq_ent.size();
+            for (int e = 0; e < cfg->n_equiv; ++e) {
+                const int32_t* r = cfg->equiv + (size_t)e * (2 + 2 * d);
+                if (r[0] == c) S.eq_ent.push_back(((r[1] * d + r[2 + k]) << 2) | r[2 + d + k]);
+            }
+        }
+        S.eq_off[(size_t)K * d] = (int32_t)S.eq_ent.size();
+    }
+    pr.n_eq_ent = (int)S.eq_ent.size();
     // Gaussian factor exp(-(p-c)²/(2σ²)) / Z written as 2^-((p-c)² gk2) / Z,
     // gk2 = log2(e) / (2σ²); σ = 0 switches it off (factor 1)
     S.zinv = 1.0;
@@ -214,6 +247,8 @@ Arena plan_arena(const Params& P)
     A.spc = take(K * 8);
     A.coff = take((K + 1) * 8);
     A.qc = take(K * 8);
+    A.eqoff = take(P.n_eq_ent > 0 ? (rows + 1) * 4 : 0);
+    A.eqent = take((size_t)P.n_eq_ent * 4);
     A.bytes = off;
     return A;
 }
@@ -242,6 +277,8 @@ void bind_arena(Params& P, unsigned char* b, const Arena& A)
     P.coff = (int64_t*)(b + A.coff);
     P.Qc = (double*)(b + A.qc);
     P.cellsum = nullptr;  // sized per pass by the context
+    P.eq_off = P.n_eq_ent > 0 ? (const int32_t*)(b + A.eqoff) : nullptr;
+    P.eq_ent = P.n_eq_ent > 0 ? (const int32_t*)(b + A.eqent) : nullptr;
 }
 
 cudaError_t upload_setup(const Params& P, const Setup& S, cudaStream_t s)
@@ -255,6 +292,10 @@ cudaError_t upload_setup(const Params& P, const Setup& S, cudaStream_t s)
         e = cudaMemcpyAsync((void*)P.pk64, S.pk64.data(), S.pk64.size(), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync((void*)P.pk32, S.pk32.data(), S.pk32.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && P.n_eq_ent > 0)
+        e = cudaMemcpyAsync((void*)P.eq_off, S.eq_off.data(), S.eq_off.size() * 4, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && P.n_eq_ent > 0)
+        e = cudaMemcpyAsync((void*)P.eq_ent, S.eq_ent.data(), S.eq_ent.size() * 4, cudaMemcpyHostToDevice, s);
     return e;
 }
 

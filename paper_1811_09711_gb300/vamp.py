@@ -53,6 +53,7 @@ class Config(C.Structure):
         ("smooth", C.c_int32), ("omega_mode", C.c_int32),
         ("gen_batch", C.c_int64), ("combine_from", C.c_int32), ("precision", C.c_int32),
         ("stratified", C.c_int32),
+        ("n_equiv", C.c_int32), ("equiv", C.POINTER(C.c_int32)),
     ]
 
 
@@ -186,6 +187,9 @@ def make_config(problem, precision: int = PREC_FP64):
     ch = _map_array(problem.channels)
     pk = _map_array(problem.peaks)
     w = np.ascontiguousarray(problem.peak_weight, np.float64)
+    eq = getattr(problem, "equivalences", None)
+    eq = (np.zeros((0, 2 + 2 * int(problem.d)), np.int32) if eq is None
+          else np.ascontiguousarray(eq, np.int32).reshape(-1, 2 + 2 * int(problem.d)))
     cfg = Config(int(problem.d), int(problem.n_channels), int(problem.n_bins),
                  C.cast(ch, C.POINTER(MapDesc)), int(problem.n_peaks),
                  w.ctypes.data_as(C.POINTER(C.c_double)), C.cast(pk, C.POINTER(MapDesc)),
@@ -193,8 +197,9 @@ def make_config(problem, precision: int = PREC_FP64):
                  int(problem.seed) & (2**64 - 1), int(problem.request_id) & 0xffffffff,
                  float(problem.grid_alpha), float(problem.beta), int(problem.n_min),
                  int(problem.smooth), int(problem.omega_mode), int(problem.gen_batch),
-                 int(problem.combine_from), int(precision), int(getattr(problem, "stratified", 0)))
-    return cfg, (ch, pk, w)
+                 int(problem.combine_from), int(precision), int(getattr(problem, "stratified", 0)),
+                 int(eq.shape[0]), eq.ctypes.data_as(C.POINTER(C.c_int32)) if eq.shape[0] else None)
+    return cfg, (ch, pk, w, eq)
 
 
 def record_bytes(d: int) -> int:
