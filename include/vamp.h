@@ -92,7 +92,8 @@ typedef struct {
  * Integrand (synthetic stand-in for the matrix element, §3.1):
  *   f(p) = Σ_q peak_weight[q] Π_k ( k mapped by peak q ? factor_q(p_k) : G(p_k) )
  *   G = Gaussian(gauss_centre, gauss_sigma) normalised on the real line or on
- *   [0,1] (gauss_norm); gauss_sigma = 0 makes G = 1. */
+ *   [0,1] (gauss_norm); gauss_sigma = 0 makes G = 1.  Peak weights may be
+ *   negative: f then takes both signs (§3.1), weights w = f/g are signed. */
 typedef struct {
     int32_t d;                  /* dimensions, 1..16 */
     int32_t n_channels;         /* K >= 1 */
@@ -134,7 +135,8 @@ typedef struct {
 /* Result of one sampling pass (§3.1 Eqs. 10-11 per channel, Eq. 23 overall).
  *   integral  = Σ_c α_c I_c, I_c = mean weight of channel c's calls
  *   variance  = Σ_c α_c^2 V_c / N_c (squared error of `integral`)
- *   w_max     = largest weight of the pass, efficiency = integral / w_max (Eq. 2)
+ *   w_max     = largest |w| of the pass, efficiency = integral / w_max (Eq. 2; for
+ *               integrands of both signs the net yield after cancellation) 
  *   combined, combined_sigma, chi2_dof: inverse-variance combination of the
  *   passes with iteration >= combine_from (0 while there are none). */
 typedef struct {
@@ -179,13 +181,15 @@ vamp_status vamp_update_alpha(vamp_ctx *ctx);
 
 /* Unweighted events from the current grids and α (§3.5 last paragraph):
  * batches of gen_batch calls, channel drawn with probability α_c, accept
- * iff u w_max < w.  w_max starts at the last pass's maximum and is raised
+ * iff u w_max < |w|; the record keeps w with its sign, so integrands of both
+ * signs (§3.1) give events of weight ±1 in units of w_max after the sign is
+ * read.  w_max starts at the last pass's maximum |w| and is raised
  * to the batch maximum between batches.  The first n_events accepted events
  * in call order are written to dev_records (device memory, caller-owned,
  * n_events * vamp_record_bytes(d) bytes, 8-byte aligned): record i =
  * { float p[d]; zero padding to 8 bytes; double w }.  Outputs (host): events
  * written, calls consumed up to the last written event, overweight events
- * (w > w_max) among them.  Synchronises.  STATE if no pass has run;
+ * (|w| > w_max) among them.  Synchronises.  STATE if no pass has run;
  * TIMEOUT if 65536 batches did not yield n_events. */
 vamp_status vamp_generate(vamp_ctx *ctx, int64_t n_events, uint32_t gen_id, void *dev_records,
                           int64_t *n_written, int64_t *n_calls_used, int64_t *n_overweight);

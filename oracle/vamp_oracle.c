@@ -39,7 +39,7 @@
  *   R10 u = (X + 1/2) 2^-32; forward bin j and fraction from (2X+1) n.
  *   R11 bin search: largest j with ξ_j <= x, clamped to [0, n-1].
  *   R12 generation: w_max from the last integration pass, raised between
- *       batches; accept iff u w_max < w; overweights counted.
+ *       batches; accept iff u w_max < |w| (R19); overweights counted.
  *   R13 per-channel sums shifted by the previous pass's channel mean.
  *   R14 synthetic integrand factors normalised on [0,1] (or the real line).
  *   R15 power map p = x^5 with p clamped to >= the smallest normal double.
@@ -64,6 +64,12 @@
  *       rebinning then keeps the axis).  All sums read the pass's own D (the
  *       equivalences act at once, not one after another), terms add in list
  *       order, and c' = c is allowed.
+ *   R19 signed integrands (§3.1 allows f < 0, e.g. at NLO): the estimators
+ *       and d-values are unchanged (D sums w² anyway); w_max is the largest
+ *       |w|; generation accepts with probability |w| / w_max and the event
+ *       keeps w with its sign; overweights are |w| > w_max.  The pass's
+ *       efficiency stays Eq. 2, ⟨w⟩ / w_max: the net yield after the signs
+ *       cancel.
  */
 #include <float.h>
 #include <math.h>
@@ -591,7 +597,7 @@ static double pass_call(pass_part *pp, int c, int64_t i, const int64_t *digit, u
     ks_add(&pp->S2[c], dv * dv);
     double w2 = w * w;
     for (int k = 0; k < d; ++k) ks_add(&pp->D[((size_t)c * d + k) * n + jf[k]], w2);
-    if (w > pp->wmax) pp->wmax = w;
+    if (fabs(w) > pp->wmax) pp->wmax = fabs(w); /* R19 */
     return dv;
 }
 
@@ -944,13 +950,13 @@ int or_generate(or_ctx *o, int64_t n_events, uint32_t gen_id, float *p_out, doub
             int c = choose_channel(o, A, unif(X[d]));
             double w = eval_call(o, c, X, NULL, 0, x, p, jf, NULL, NULL, NULL);
             if (!isfinite(w)) { rc = OR_ERR_NUMERIC; w = 0.0; }
-            if (w > bmax) bmax = w;
+            if (fabs(w) > bmax) bmax = fabs(w);
             if (written < n_events) {
                 ++used;
-                if (unif(X[d + 1]) * wm < w) {
+                if (unif(X[d + 1]) * wm < fabs(w)) { /* R19: keep the sign */
                     for (int k = 0; k < d; ++k) p_out[written * d + k] = (float)p[k];
                     w_out[written] = w;
-                    if (w > wm) ++over;
+                    if (fabs(w) > wm) ++over;
                     ++written;
                 }
             }

@@ -444,7 +444,7 @@ __global__ void k_gen_copy(Params P, PassArgs G, unsigned char* out)
     for (long long r = threadIdx.x; r < ncopy; r += blockDim.x) {
         const double w = *reinterpret_cast<const double*>(G.staging + ((int64_t)b * G.chunk + r) * G.rec_bytes +
                                                           (G.rec_bytes - 8));
-        over += (w > wmax);
+        over += (fabs(w) > wmax);
     }
     if (over) atomicAdd(reinterpret_cast<unsigned long long*>(&P.sc->gen_over), (unsigned long long)over);
 }

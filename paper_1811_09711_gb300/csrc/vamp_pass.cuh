@@ -13,7 +13,7 @@
 //      with the channels' lookup blocks streamed through shared memory in
 //      tiles (cp.async.bulk, two buffers, bounded mbarrier waits);
 //   C  w = f/g: per-channel shifted sums, d-values D_{c,k,j} += w² (Eq. 15),
-//      max weight (integration); accept u w_max < w and ordered compaction
+//      max |weight| (integration); accept u w_max < |w| and ordered compaction
 //      of the event records (generation).
 #pragma once
 
@@ -181,7 +181,7 @@ __device__ __forceinline__ void phase_c_int(const SH& sh, const Calls<T, CPT, SH
         s2 += dv * dv;
         if (cs.sum)  // stratified: the sum of the call's cell
             atomicAdd(&cs.sum[cs.coff + (cs.l0 + q * PASS_THREADS + (int)threadIdx.x) / cs.spc], dv);
-        wm = fmax(wm, w);
+        wm = fmax(wm, fabs(w));  // signed integrands: w_max bounds |w|
         const double w2 = w * w;
 #pragma unroll
         for (int s = 0; s < DM; ++s) {
@@ -373,8 +373,8 @@ __global__ void __launch_bounds__(PASS_THREADS, MINB) k_pass(Params P, PassArgs 
                 if (C.valid[q]) {
                     w = C.g[q] > T(0) ? (double)(C.f[q] / C.g[q]) : 0.0;
                     if (!isfinite(w)) { bad = true; w = 0.0; }
-                    wm = fmax(wm, w);
-                    acc = unif64(C.xacc[q]) * wmax < w;
+                    wm = fmax(wm, fabs(w));
+                    acc = unif64(C.xacc[q]) * wmax < fabs(w);  // the event keeps the sign of w
                 }
                 const unsigned bal = __ballot_sync(0xffffffffu, acc);
                 if (lane == 0) H.wcnt[wid] = __popc(bal);

@@ -24,6 +24,8 @@ integrands stand in for them:
   channels log-uniform in 1..64, calls log-uniform in 1e4..1e7, bins in
   {20, 50, 100}), each built like ``bw_gauss``.
 * ``serving_stream``: Poisson arrivals of integrate-then-generate requests.
+* ``signed_pair`` / ``signed_bw_gauss``: integrands of both signs (peaks
+  with negative weights), as NLO matrix elements can be (§3.1).
 * ``ring``: channels that are images of one another under a cyclic shift
   of coordinates (and mirror-symmetric on every axis), with the channel
   equivalences that say so (§3.5).
@@ -301,6 +303,32 @@ def special_case(kind: str, d: int = 2, n_bins: int = 10, seed: int = 7,
                    peak_weight=np.ones(1), peaks=pk, gauss_sigma=0.0,
                    gauss_centre=0.5, gauss_norm=GAUSS_NORM_UNIT, seed=seed,
                    iterations=3, calls=5000, adapt_grid=True, adapt_alpha=False)
+
+
+def signed_pair(weights=(1.3, -0.3), d: int = 1, masses=(0.3, 0.7), width: float = 0.05,
+                seed: int = 13) -> Problem:
+    """f = w_0 BW(p_0; m_0) + w_1 BW(p_0; m_1) (factor 1 on other coordinates),
+    two channels with the matching Breit-Wigner maps.  A negative weight makes
+    f < 0 around its mass; the integral is w_0 + w_1."""
+    ms = MapSet.identity(2)
+    ms.n_mapped[:] = 1
+    ms.coord[:, 0] = 0
+    ms.kind[:, 0] = MAP_BW
+    ms.a[:, 0] = masses
+    ms.b[:, 0] = width
+    return Problem(name=f"signed_pair_d{d}", d=d, n_bins=20, channels=ms,
+                   peak_weight=np.asarray(weights, np.float64), peaks=ms.copy(),
+                   gauss_sigma=0.0, gauss_centre=0.5, gauss_norm=GAUSS_NORM_UNIT, seed=seed,
+                   iterations=5, calls=20_000, adapt_grid=True, adapt_alpha=True, combine_from=2)
+
+
+def signed_bw_gauss(problem_seed: int = 2, rng_seed: int = 2) -> Problem:
+    """``bw_gauss`` with the last peak's weight negated: f < 0 near its
+    resonance; the integral is the signed sum of the weights."""
+    pr = bw_gauss(problem_seed, rng_seed)
+    w = np.array(pr.peak_weight)
+    w[5] *= -1.0
+    return pr.replace(name="signed_bw_gauss_d8_k6", peak_weight=w)
 
 
 def ring(n_ring: int = 3, d: int = 6, width: float = 3e-3, seed: int = 11,

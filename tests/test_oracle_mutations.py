@@ -61,7 +61,7 @@ MUTATIONS = [
      "forward_map_uniform_grid"),
     ("channel_choice_reflected", "double tgt = u * A[o->K - 1];",
      "double tgt = (1.0 - u) * A[o->K - 1];", "channel_choice_is_inverse_cdf"),
-    ("accept_inverted", "if (unif(X[d + 1]) * wm < w) {", "if (unif(X[d + 1]) * wm > w) {",
+    ("accept_inverted", "if (unif(X[d + 1]) * wm < fabs(w)) {", "if (unif(X[d + 1]) * wm > fabs(w)) {",
      "generation_brute_force"),
     # pseudo-stratified mode (R16, R17): pins in test_oracle_stratified.py
     ("strat_variance_no_bessel", "V = (ks_val(&s2) - ks_val(&qq) / s) / ((double)o->Cc[c] * (s - 1.0));",
@@ -89,6 +89,15 @@ MUTATIONS = [
      "test_oracle_equiv.py"),
     ("eq_invariant_adds_one", "for (int j = 0; j < n; ++j) out[j] = 1.0;",
      "for (int j = 0; j < n; ++j) out[j] += 1.0;", "invariant_axis", "test_oracle_equiv.py"),
+    # signed integrands (R19): pins in test_oracle_signed.py
+    ("signed_wmax_not_abs", "if (fabs(w) > pp->wmax) pp->wmax = fabs(w); /* R19 */",
+     "if (w > pp->wmax) pp->wmax = w;", "largest_abs_weight", "test_oracle_signed.py"),
+    ("signed_accept_not_abs", "if (unif(X[d + 1]) * wm < fabs(w)) { /* R19: keep the sign */",
+     "if (unif(X[d + 1]) * wm < w) {", "follow_abs_f", "test_oracle_signed.py"),
+    ("signed_batch_max_not_abs", "if (fabs(w) > bmax) bmax = fabs(w);", "if (w > bmax) bmax = w;",
+     "raises_w_max", "test_oracle_signed.py"),
+    ("signed_event_loses_sign", "w_out[written] = w;", "w_out[written] = fabs(w);",
+     "follow_abs_f", "test_oracle_signed.py"),
 ]
 
 
