@@ -220,10 +220,16 @@ def run_batch(V, P, n_inst: int, iters: int):
         b.iterate(nc, 0)  # tuning (if any) and graph capture
         t = time.perf_counter()
         calls = 0
+        ops = 0.0
         for it in range(1, iters + 1):
-            calls += sum(r.n_calls for r in b.iterate(nc, it))
+            res = b.iterate(nc, it)
+            calls += sum(r.n_calls for r in res)
+            ops += sum(r.n_calls * algorithmic_ops_per_call(p) for r, p in zip(res, probs))
         dt = time.perf_counter() - t
-        out[tag] = {"calls_per_s": calls / dt, "ms_per_iteration": 1e3 * dt / iters}
+        # algorithmic lane-ops of every instance's calls (each charged with its
+        # own K, d and mapped coordinates) over the whole iteration's wall time
+        out[tag] = {"calls_per_s": calls / dt, "ms_per_iteration": 1e3 * dt / iters,
+                    "alu_ops_per_s": ops / dt}
         if tune:
             out["tuning"] = b.tuning()
         b.close()
@@ -488,6 +494,9 @@ def run_gpu(args):
             "ops_per_call": algorithmic_ops_per_call(pr),
             "frac_lookups_only": lookup_ops_per_call(pr) * (calls / max(args.steps, 1)) / (k_ms / 1e3) / 1e12 / peak_tops,
             "peak_source": f"{n_sm} SMs x 128 lanes x {sm_max:.0f} MHz ({src} max clock)"}
+    if batch is not None:
+        for tag in ("tuned", "fixed"):
+            batch[tag]["frac_of_alu_peak"] = batch[tag]["alu_ops_per_s"] / (peak_tops * 1e12)
 
     res = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
