@@ -96,13 +96,14 @@ __global__ void k_begin_pass(Params P, int64_t N)
 // ---------------------------------------------------------------------------
 // pass result (Eqs. 10, 11 per channel on shifted sums; Eq. 23; R8, R9)
 // ---------------------------------------------------------------------------
+// Called by every thread of one block: per-channel values in parallel, then
+// thread 0 sums them in channel order (the order of the scalar form).
 __device__ void finish_pass_dev(const Params& P, int combine)
 {
     Scalars* sc = P.sc;
-    double I = 0.0, V = 0.0;
-    for (int c = 0; c < P.K; ++c) {
+    for (int c = threadIdx.x; c < P.K; c += blockDim.x) {
         const int64_t nci = P.Nc[c];
-        if (nci == 0) { P.Ic[c] = P.Vc[c] = P.Wc[c] = 0.0; continue; }
+        if (nci == 0) { P.Ic[c] = P.Vc[c] = P.Wc[c] = 0.0; P.shift[c] = 0.0; continue; }
         const double Nc = (double)nci;
         const double m1 = P.csum[2 * c] / Nc, m2 = P.csum[2 * c + 1] / Nc;
         const double Ic = P.shift[c] + m1;
@@ -118,13 +119,16 @@ __device__ void finish_pass_dev(const Params& P, int combine)
         P.Ic[c] = Ic;
         P.Vc[c] = Vv;
         P.Wc[c] = (m2 - m1 * m1) + Ic * Ic;
+        P.shift[c] = Ic;  // R13: the next pass's sums are taken about this mean
     }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    double I = 0.0, V = 0.0;
     for (int c = 0; c < P.K; ++c) {
         if (P.Nc[c] == 0) continue;
         I += P.alpha[c] * P.Ic[c];
         V += P.alpha[c] * P.alpha[c] * P.Vc[c] / (double)P.Nc[c];
     }
-    for (int c = 0; c < P.K; ++c) P.shift[c] = P.Ic[c];
     const double wmax = __longlong_as_double((long long)sc->wmax_bits);
     sc->wmax_gen = wmax;
     const int h = sc->n_hist;
@@ -176,7 +180,7 @@ __device__ void finish_pass_dev(const Params& P, int combine)
 
 __global__ void k_finish_pass(Params P, int combine)
 {
-    if (threadIdx.x == 0 && blockIdx.x == 0) finish_pass_dev(P, combine);
+    finish_pass_dev(P, combine);
 }
 
 // ---------------------------------------------------------------------------
@@ -348,37 +352,56 @@ __global__ void __launch_bounds__(REFINE_WARPS * 32) k_refine(Params P)
 // ---------------------------------------------------------------------------
 // channel weights (Eq. 25 with R5)
 // ---------------------------------------------------------------------------
+// Called by every thread of one block: the channel terms α_c ω_c^β in
+// parallel (kept in Acum), the sums SU, MU and the normalisation by thread 0
+// in channel order (the order of the scalar form).
 __device__ void update_alpha_dev(const Params& P)
 {
+    __shared__ double red[2];
     const int K = P.K;
-    double SU = 0.0, MU = 0.0;
-    for (int c = 0; c < K; ++c) {
-        const double om = P.omega_mode ? P.Wc[c] : P.Vc[c];
-        if (P.alpha[c] > 0.0 && P.Nc[c] > 0 && om > 0.0) {
-            SU += P.alpha[c] * pow(om, P.beta);
-            MU += P.alpha[c];
+    auto omega = [&](int c) { return P.omega_mode ? P.Wc[c] : P.Vc[c]; };
+    auto live = [&](int c) { return P.alpha[c] > 0.0 && P.Nc[c] > 0 && omega(c) > 0.0; };
+    for (int c = threadIdx.x; c < K; c += blockDim.x)
+        P.Acum[c] = live(c) ? P.alpha[c] * pow(omega(c), P.beta) : 0.0;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double SU = 0.0, MU = 0.0;
+        for (int c = 0; c < K; ++c) {
+            if (live(c)) {
+                SU += P.Acum[c];
+                MU += P.alpha[c];
+            }
         }
+        red[0] = SU;
+        red[1] = MU;
     }
-    double tot = 0.0;
-    // new weights go to Acum as scratch first
-    for (int c = 0; c < K; ++c) {
-        const double om = P.omega_mode ? P.Wc[c] : P.Vc[c];
+    __syncthreads();
+    const double SU = red[0], MU = red[1];
+    for (int c = threadIdx.x; c < K; c += blockDim.x) {
         double a = P.alpha[c];
         if (a > 0.0 && P.Nc[c] > 0) {
-            if (om > 0.0) a = P.alpha[c] * pow(om, P.beta) / SU * MU;
-            else if (P.Ic[c] == 0.0) a = 0.0;
+            if (omega(c) > 0.0) a = P.Acum[c] / SU * MU;
+            else if (P.Ic[c] == 0.0) a = 0.0;  // every call of the channel gave w = 0
         }
-        P.Acum[c] = a;
-        tot += a;
+        P.Acum[c] = a;  // new weights, normalised below
     }
-    if (tot > 0.0)
-        for (int c = 0; c < K; ++c) P.alpha[c] = P.Acum[c] / tot;
-    for (int c = 0; c < K; ++c) P.alpha32[c] = (float)P.alpha[c];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tot = 0.0;
+        for (int c = 0; c < K; ++c) tot += P.Acum[c];
+        red[0] = tot;
+    }
+    __syncthreads();
+    const double tot = red[0];
+    for (int c = threadIdx.x; c < K; c += blockDim.x) {
+        if (tot > 0.0) P.alpha[c] = P.Acum[c] / tot;
+        P.alpha32[c] = (float)P.alpha[c];
+    }
 }
 
 __global__ void k_update_alpha(Params P)
 {
-    if (threadIdx.x == 0 && blockIdx.x == 0) update_alpha_dev(P);
+    update_alpha_dev(P);
 }
 
 // ---------------------------------------------------------------------------
@@ -575,12 +598,14 @@ __global__ void k_batch_items(MultiArgs M)
     }
 }
 
+// one block per instance
 __global__ void k_batch_finish(MultiArgs M)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.x;
     if (i >= M.n_inst) return;
     const Params& P = M.inst[i];
     finish_pass_dev(P, (int)M.iter[i] >= M.combine_from[i] ? 1 : 0);
+    if (threadIdx.x != 0) return;
     double* r = M.results + (size_t)i * 9;
     for (int q = 0; q < 8; ++q) r[q] = P.sc->res[q];
     r[4] = (double)P.sc->n_total;
@@ -602,10 +627,11 @@ __global__ void __launch_bounds__(REFINE_WARPS * 32) k_batch_refine(MultiArgs M)
     refine_row_dev(M.inst[lo], row - M.row_off[lo], lane, rs + (size_t)wid * (4 * M.max_n + 2));
 }
 
+// one block per instance
 __global__ void k_batch_alpha(MultiArgs M)
 {
     if (!(M.it->adapt & 2)) return;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.x;
     if (i < M.n_inst) update_alpha_dev(M.inst[i]);
 }
 
@@ -620,14 +646,14 @@ cudaError_t launch_batch_begin(const MultiArgs& M, cudaStream_t s)
 
 cudaError_t launch_batch_after(const MultiArgs& M, cudaStream_t s)
 {
-    k_batch_finish<<<(M.n_inst + 63) / 64, 64, 0, s>>>(M);
+    k_batch_finish<<<M.n_inst, 64, 0, s>>>(M);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int blocks = (M.nrows + REFINE_WARPS - 1) / REFINE_WARPS;
     k_batch_refine<<<blocks, REFINE_WARPS * 32, (size_t)REFINE_WARPS * (4 * M.max_n + 2) * sizeof(double), s>>>(M);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_batch_alpha<<<(M.n_inst + 63) / 64, 64, 0, s>>>(M);
+    k_batch_alpha<<<M.n_inst, 64, 0, s>>>(M);
     return cudaGetLastError();
 }
 
@@ -676,7 +702,7 @@ cudaError_t launch_strat_q(const Params& P, cudaStream_t s)
 
 cudaError_t launch_finish_pass(const Params& P, int combine, cudaStream_t s)
 {
-    k_finish_pass<<<1, 32, 0, s>>>(P, combine);
+    k_finish_pass<<<1, 256, 0, s>>>(P, combine);
     return cudaGetLastError();
 }
 
@@ -699,7 +725,7 @@ cudaError_t launch_refine(const Params& P, cudaStream_t s)
 
 cudaError_t launch_update_alpha(const Params& P, cudaStream_t s)
 {
-    k_update_alpha<<<1, 32, 0, s>>>(P);
+    k_update_alpha<<<1, 256, 0, s>>>(P);
     return cudaGetLastError();
 }
 
