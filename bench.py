@@ -43,6 +43,7 @@ import subprocess
 import sys
 import threading
 import time
+import types
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
@@ -142,6 +143,11 @@ def job_throughput(t_ms: float, calls: float, world_size: int, device="cpu"):
 
 
 KERNEL_SOURCES = ["vamp_pass.cuh", "vamp_device.cuh", "vamp_pass_f32_shapes.cu", "vamp_internal.h"]
+
+
+# kernels of one timed adaptation step: allocation, sampling pass, pass
+# result, result copy (asynchronous form), rebinning, channel weights
+KERNELS_PER_STEP = 6
 
 
 def measured_traffic(kernel: str):
@@ -350,23 +356,33 @@ def run_gpu(args):
             dist.barrier()
 
     def timed_steps(g, n_steps, it0, fp):
-        """Runs n_steps adaptation iterations; returns per-step ms and calls."""
-        ms, calls = [], 0
+        """Runs n_steps adaptation iterations (asynchronous passes: no host
+        round trip between steps; each pass's result lands in device memory
+        and is read after the last step); returns per-step ms, calls and the
+        last pass's result."""
+        ms = []
+        res = torch.zeros((n_steps, 9), dtype=torch.float64, device=dev)
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_steps)]
+        torch.cuda.synchronize()
         for s in range(n_steps):
             with torch.cuda.stream(stream):
                 flush.zero_()  # L2 flush outside the timed events
                 ev[s][0].record(stream)
-            r = g.sample_pass(N, it0 + s)
+            g.sample_pass_async(N, it0 + s, res[s].data_ptr())
             g.refine_grids()
             g.update_alpha()
             with torch.cuda.stream(stream):
                 ev[s][1].record(stream)
-            calls += r.n_calls
         stream.synchronize()
         for a, b in ev:
             ms.append(a.elapsed_time(b))
-        return ms, calls, r
+        rows = res.cpu().numpy()
+        if rows[:, 8].any():
+            raise RuntimeError("a timed pass raised a device error flag")
+        last = types.SimpleNamespace(**dict(zip(
+            ("integral", "variance", "w_max", "efficiency", "n_calls", "combined", "combined_sigma", "chi2_dof"),
+            (float(v) for v in rows[-1, :8]))))
+        return ms, int(rows[:, 4].sum()), last
 
     # ---- FP32-eval: headline -------------------------------------------------
     g = V.Vamp(pr, precision=V.PREC_FP32_EVAL, stream=stream)
@@ -512,7 +528,7 @@ def run_gpu(args):
            "last_pass": {"integral": last.integral, "sigma": math.sqrt(max(last.variance, 0.0)),
                          "efficiency": last.efficiency, "combined": last.combined,
                          "combined_sigma": last.combined_sigma, "chi2_dof": last.chi2_dof},
-           "e2e": e2e, "gpu_launches": 5 * args.steps, "roofline": roof, "clocks": clk}
+           "e2e": e2e, "gpu_launches": KERNELS_PER_STEP * args.steps, "roofline": roof, "clocks": clk}
     if batch is not None:
         res["batch"] = batch
     if serving is not None:

@@ -168,6 +168,20 @@ vamp_status vamp_create(const vamp_config *cfg, void *cuda_stream, vamp_ctx **ou
 vamp_status vamp_sample_pass(vamp_ctx *ctx, int64_t n_calls, uint32_t iteration,
                              vamp_pass_result *out);
 
+/* Asynchronous form of vamp_sample_pass: enqueues the same pass on the
+ * context's stream and returns without waiting.  When the stream reaches it,
+ * dev_out (caller-owned device memory, 8-byte aligned, 9 doubles) receives
+ * integral, variance, w_max, efficiency, n_calls, combined, combined_sigma,
+ * chi2_dof (as in vamp_pass_result) and the device error flags (0: none;
+ * non-zero: a non-finite weight or a wait that gave up, which the next
+ * vamp_sample_pass or vamp_generate also reports and clears).  A context's
+ * first pass picks its kernel by timing the candidates and synchronises;
+ * once a pass of at least as many calls has run, the call allocates nothing
+ * and only launches kernels and memsets, so an adaptation iteration
+ * (this call, vamp_refine_grids, vamp_update_alpha) can be captured in a CUDA
+ * graph.  Errors: INVALID_ARG as vamp_sample_pass, or for dev_out. */
+vamp_status vamp_sample_pass_async(vamp_ctx *ctx, int64_t n_calls, uint32_t iteration, double *dev_out);
+
 /* Rebins every (channel, axis) grid from the last pass's d-values (Eqs. 14,
  * 15): ω_j = sqrt(D_j), r_j = ω_j / Σ ω, m_j = ((r_j - 1)/ln r_j)^grid_alpha;
  * new edges invert the cumulative of m, linear inside each old bin.
@@ -248,7 +262,9 @@ vamp_status vamp_allocate(vamp_ctx *ctx, int64_t n_calls, int64_t *n_total);
 /* Kernel timing for benchmarks: with enable = 1 the context records CUDA
  * events on its stream around every launch of the sampling kernel and of the
  * generation kernel; vamp_kernel_stats returns the summed device time (ms)
- * and the launch counts since the last enable.  Off by default. */
+ * and the launch counts since the last enable (it synchronises the stream
+ * when asynchronous passes are still pending; passes enqueued during a
+ * stream capture are not timed).  Off by default. */
 vamp_status vamp_profile(vamp_ctx *ctx, int32_t enable);
 
 /* Self-test of the device-side bounded wait that every staged-tile wait of

@@ -53,6 +53,9 @@ struct vamp_ctx {
     cudaEvent_t ev[2] = {nullptr, nullptr};
     double prof_sample_ms = 0.0, prof_gen_ms = 0.0;
     int64_t prof_sample_n = 0, prof_gen_n = 0;
+    // event pairs around asynchronous passes, read by vamp_kernel_stats
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_pending;
+    std::vector<cudaEvent_t> ev_pool;
     std::string err;
 };
 
@@ -266,6 +269,8 @@ void vamp_destroy(vamp_ctx* c)
         cudaFreeHost(c->h_head);
         if (c->ev[0]) cudaEventDestroy(c->ev[0]);
         if (c->ev[1]) cudaEventDestroy(c->ev[1]);
+        for (auto& pr : c->prof_pending) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
+        for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     }
     delete c;
 }
@@ -349,10 +354,12 @@ vamp_status vamp_allocate(vamp_ctx* c, int64_t n_calls, int64_t* n_total)
     return VAMP_OK;
 }
 
-vamp_status vamp_sample_pass(vamp_ctx* c, int64_t n_calls, uint32_t iteration, vamp_pass_result* out)
+namespace {
+
+// Checks, buffer sizing, kernel choice and the launches of one sampling pass
+// (allocation, pass, stratified cell sums, result); nothing waits for them.
+vamp_status enqueue_pass(vamp_ctx* c, int64_t n_calls, uint32_t iteration, cudaEvent_t e0, cudaEvent_t e1)
 {
-    if (!c) return VAMP_ERR_INVALID_ARG;
-    if (!out) return fail(c, VAMP_ERR_INVALID_ARG, "out is required");
     if (n_calls < 1) return fail(c, VAMP_ERR_INVALID_ARG, "n_calls must be >= 1");
     if (iteration >= 0x80000000u) return fail(c, VAMP_ERR_INVALID_ARG, "iteration must be < 2^31");
     if (n_calls + (int64_t)c->K * c->prm.n_min > int64_t(0xffffffff))
@@ -381,12 +388,24 @@ vamp_status vamp_sample_pass(vamp_ctx* c, int64_t n_calls, uint32_t iteration, v
     VAMP_CK(c, cudaMemsetAsync(P.csum, 0, (size_t)2 * c->K * 8, c->stream));
     if (P.stratified) VAMP_CK(c, cudaMemsetAsync(P.cellsum, 0, (size_t)max_cells * 8, c->stream));
     VAMP_CK(c, vamp::launch_begin_pass(P, n_calls, c->stream));
-    if (c->prof) VAMP_CK(c, cudaEventRecord(c->ev[0], c->stream));
+    if (e0) VAMP_CK(c, cudaEventRecord(e0, c->stream));
     VAMP_CK(c, c->var->launch(P, 0, pass_args(c, iteration), c->grid_pass, c->smem_pass, c->stream));
-    if (c->prof) VAMP_CK(c, cudaEventRecord(c->ev[1], c->stream));
+    if (e1) VAMP_CK(c, cudaEventRecord(e1, c->stream));
     if (P.stratified) VAMP_CK(c, vamp::launch_strat_q(P, c->stream));
     VAMP_CK(c, vamp::launch_finish_pass(P, (int)iteration >= c->combine_from ? 1 : 0, c->stream));
-    vamp_status s = read_head(c);
+    return VAMP_OK;
+}
+
+}  // namespace
+
+vamp_status vamp_sample_pass(vamp_ctx* c, int64_t n_calls, uint32_t iteration, vamp_pass_result* out)
+{
+    if (!c) return VAMP_ERR_INVALID_ARG;
+    if (!out) return fail(c, VAMP_ERR_INVALID_ARG, "out is required");
+    DeviceGuard g(c->dev);
+    vamp_status s = enqueue_pass(c, n_calls, iteration, c->prof ? c->ev[0] : nullptr, c->prof ? c->ev[1] : nullptr);
+    if (s != VAMP_OK) return s;
+    s = read_head(c);
     if (s != VAMP_OK) return s;
     if (c->prof) {
         float ms = 0.f;
@@ -405,6 +424,29 @@ vamp_status vamp_sample_pass(vamp_ctx* c, int64_t n_calls, uint32_t iteration, v
     out->chi2_dof = h->res[7];
     c->have_pass = 1;
     return take_numeric_flag(c);
+}
+
+vamp_status vamp_sample_pass_async(vamp_ctx* c, int64_t n_calls, uint32_t iteration, double* dev_out)
+{
+    if (!c) return VAMP_ERR_INVALID_ARG;
+    if (!dev_out || ((uintptr_t)dev_out & 7u)) return fail(c, VAMP_ERR_INVALID_ARG, "dev_out must be 8-byte aligned device memory");
+    DeviceGuard g(c->dev);
+    // kernel timing (vamp_profile) only outside a stream capture
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    VAMP_CK(c, cudaStreamIsCapturing(c->stream, &cap));
+    cudaEvent_t e[2] = {nullptr, nullptr};
+    if (c->prof && cap == cudaStreamCaptureStatusNone) {
+        for (int q = 0; q < 2; ++q) {
+            if (!c->ev_pool.empty()) { e[q] = c->ev_pool.back(); c->ev_pool.pop_back(); }
+            else VAMP_CK(c, cudaEventCreate(&e[q]));
+        }
+        c->prof_pending.emplace_back(e[0], e[1]);
+    }
+    vamp_status s = enqueue_pass(c, n_calls, iteration, e[0], e[1]);
+    if (s != VAMP_OK) return s;
+    VAMP_CK(c, vamp::launch_pass_result(c->prm, dev_out, c->stream));
+    c->have_pass = 1;
+    return VAMP_OK;
 }
 
 vamp_status vamp_refine_grids(vamp_ctx* c)
@@ -708,6 +750,9 @@ vamp_status vamp_profile(vamp_ctx* c, int32_t enable)
     c->prof = enable ? 1 : 0;
     c->prof_sample_ms = c->prof_gen_ms = 0.0;
     c->prof_sample_n = c->prof_gen_n = 0;
+    if (!c->prof_pending.empty()) VAMP_CK(c, cudaStreamSynchronize(c->stream));
+    for (auto& pr : c->prof_pending) { c->ev_pool.push_back(pr.first); c->ev_pool.push_back(pr.second); }
+    c->prof_pending.clear();
     return VAMP_OK;
 }
 
@@ -715,6 +760,19 @@ vamp_status vamp_kernel_stats(vamp_ctx* c, double* sample_ms, int64_t* sample_la
                               int64_t* gen_launches)
 {
     if (!c) return VAMP_ERR_INVALID_ARG;
+    if (!c->prof_pending.empty()) {
+        DeviceGuard g(c->dev);
+        VAMP_CK(c, cudaStreamSynchronize(c->stream));
+        for (auto& pr : c->prof_pending) {
+            float ms = 0.f;
+            VAMP_CK(c, cudaEventElapsedTime(&ms, pr.first, pr.second));
+            c->prof_sample_ms += ms;
+            c->prof_sample_n += 1;
+            c->ev_pool.push_back(pr.first);
+            c->ev_pool.push_back(pr.second);
+        }
+        c->prof_pending.clear();
+    }
     if (sample_ms) *sample_ms = c->prof_sample_ms;
     if (sample_launches) *sample_launches = c->prof_sample_n;
     if (gen_ms) *gen_ms = c->prof_gen_ms;

@@ -142,6 +142,7 @@ cudaError_t launch_strat_q(const Params& P, cudaStream_t s);  // stratified pass
 cudaError_t launch_derive(const Params& P, cudaStream_t s);
 cudaError_t launch_refine(const Params& P, cudaStream_t s);
 cudaError_t launch_update_alpha(const Params& P, cudaStream_t s);
+cudaError_t launch_pass_result(const Params& P, double* out, cudaStream_t s);  // 9 doubles
 cudaError_t launch_gen_prepare(const Params& P, cudaStream_t s);
 cudaError_t launch_gen_finish(const Params& P, const PassArgs& G, int64_t remaining, unsigned char* out,
                               cudaStream_t s);

@@ -183,6 +183,17 @@ __global__ void k_finish_pass(Params P, int combine)
     finish_pass_dev(P, combine);
 }
 
+// Result of the last pass into a caller's device array (asynchronous form):
+// integral, variance, w_max, efficiency, N', combined, its σ, χ²/dof, flags.
+__global__ void k_pass_result(Params P, double* out)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const Scalars* sc = P.sc;
+    for (int q = 0; q < 8; ++q) out[q] = sc->res[q];
+    out[4] = (double)sc->n_total;
+    out[8] = (double)sc->err;
+}
+
 // ---------------------------------------------------------------------------
 // lookup blocks of one grid row (Eq. 12 densities, FP32 copies, cell tables)
 // ---------------------------------------------------------------------------
@@ -720,6 +731,12 @@ cudaError_t launch_refine(const Params& P, cudaStream_t s)
     const int blocks = (rows + REFINE_WARPS - 1) / REFINE_WARPS;
     const size_t sm = (size_t)REFINE_WARPS * (4 * P.n + 2) * sizeof(double);
     k_refine<<<blocks, REFINE_WARPS * 32, sm, s>>>(P);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pass_result(const Params& P, double* out, cudaStream_t s)
+{
+    k_pass_result<<<1, 32, 0, s>>>(P, out);
     return cudaGetLastError();
 }
 

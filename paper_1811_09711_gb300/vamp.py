@@ -92,6 +92,8 @@ def load():
         lib.vamp_create.restype = st
         lib.vamp_sample_pass.argtypes = [vp, i64, u32, C.POINTER(PassResult)]
         lib.vamp_sample_pass.restype = st
+        lib.vamp_sample_pass_async.argtypes = [vp, i64, u32, vp]
+        lib.vamp_sample_pass_async.restype = st
         lib.vamp_refine_grids.argtypes = [vp]
         lib.vamp_refine_grids.restype = st
         lib.vamp_update_alpha.argtypes = [vp]
@@ -255,6 +257,12 @@ class Vamp:
         out = PassResult()
         self._check(self.lib.vamp_sample_pass(self.h, int(n_calls), int(iteration), C.byref(out)))
         return out
+
+    def sample_pass_async(self, n_calls: int, iteration: int, dev_out_ptr: int):
+        """vamp_sample_pass_async: enqueues the pass; 9 doubles land at the
+        device address dev_out_ptr (integral, variance, w_max, efficiency,
+        n_calls, combined, combined_sigma, chi2_dof, error flags)."""
+        self._check(self.lib.vamp_sample_pass_async(self.h, int(n_calls), int(iteration), C.c_void_p(dev_out_ptr)))
 
     def refine_grids(self):
         self._check(self.lib.vamp_refine_grids(self.h))
