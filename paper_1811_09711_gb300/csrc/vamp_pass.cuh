@@ -388,12 +388,15 @@ __global__ void __launch_bounds__(PASS_THREADS, MINB) k_pass(Params P, PassArgs 
                 if (acc) {
                     const int pos = running + H.woff[wid] + __popc(bal & ((1u << lane) - 1u));
                     const int64_t slot = cbase + pos;
+                    // record {float p[d]; zero pad to 8 bytes; double w}: 8-byte
+                    // stores (records are 8-byte multiples at 8-byte offsets)
                     unsigned char* rec = A.staging + slot * A.rec_bytes;
-                    float* pf = reinterpret_cast<float*>(rec);
+                    float2* pf2 = reinterpret_cast<float2*>(rec);
 #pragma unroll
-                    for (int k = 0; k < DM; ++k)
-                        if (sh.has(k)) pf[k] = (float)C.p[q][k];
-                    if (d & 1) pf[d] = 0.0f;
+                    for (int k = 0; k < DM; k += 2)
+                        if (sh.has(k))
+                            pf2[k >> 1] = make_float2((float)C.p[q][k],
+                                                      (k + 1 < DM && sh.has(k + 1)) ? (float)C.p[q][k + 1] : 0.0f);
                     *reinterpret_cast<double*>(rec + A.rec_bytes - 8) = w;
                     A.callidx[slot] = (uint32_t)(base + (int64_t)q * PASS_THREADS + tid);
                 }

@@ -5,6 +5,20 @@ kernels of ``libvamp_gb300.so``.  There is no CPU fallback -- if the library
 is missing or no GPU is present, :func:`load` raises.
 
 PyTorch is used only for device memory (event-record buffers) and streams.
+
+A typical run (the adaptation loop of §3.5, then unweighted events)::
+
+    from paper_1811_09711_gb300 import problems, vamp
+    pr = problems.collider()
+    g = vamp.Vamp(pr, precision=vamp.PREC_FP32_EVAL)
+    for it in range(pr.iterations):
+        r = g.sample_pass(pr.calls, it)   # estimate, variance, w_max (Eqs. 23, 31)
+        g.refine_grids()                  # rebinning (Eqs. 14, 15)
+        g.update_alpha()                  # channel weights (Eq. 25)
+    p, w, stats = g.generate_torch(10_000)   # unweighted events (§2)
+
+Many problems at once: :class:`Batch`; a request stream: :class:`Server`;
+graph-capturable iterations: :meth:`Vamp.sample_pass_async`.
 """
 from __future__ import annotations
 
