@@ -20,10 +20,18 @@ def _iterate(g, n, it0, iters):
     return r
 
 
-@pytest.mark.parametrize("precision,tol", [(0, 1e-12), (1, 1e-9)])
-def test_restored_run_continues_the_uninterrupted_run(precision, tol):
+def _modes_problem():
+    """Pseudo-stratified, with symmetric channel equivalences and a peak of
+    negative weight."""
+    return P.ring(3, 5, kind=P.EQ_SYMMETRIC).replace(peak_weight=np.array([1.4, -0.6, 0.2]), stratified=1,
+                                                      combine_from=1, n_bins=16)
+
+
+@pytest.mark.parametrize("precision,tol,factory", [(0, 1e-12, "bw_gauss"), (1, 1e-9, "bw_gauss"),
+                                                   (0, 1e-12, "modes")])
+def test_restored_run_continues_the_uninterrupted_run(precision, tol, factory):
     from paper_1811_09711_gb300 import vamp as V
-    pr = P.bw_gauss().replace(combine_from=1)
+    pr = P.bw_gauss().replace(combine_from=1) if factory == "bw_gauss" else _modes_problem()
     n = 100_000
     full = V.Vamp(pr, precision=precision)
     rf = _iterate(full, n, 0, 5)
