@@ -633,3 +633,22 @@ def test_generation_channel_choice_is_inverse_cdf(oracle_mod):
         u = (float(r["words"][pr.d]) + 0.5) * 2.0 ** -32
         c = r["channel"]
         assert u * A[-1] < A[c] and (c == 0 or u * A[-1] >= A[c - 1])
+
+
+@pytest.mark.parametrize("factory,calls", [(P.bw_gauss, 60_000), (P.collider, 6_000)])
+def test_thread_split_is_exact(oracle_mod, factory, calls):
+    """The oracle's multi-threaded pass (contiguous call chunks, ordered merge
+    of compensated partial sums) equals its single-threaded pass."""
+    pr = factory()
+    a, b = oracle_mod.Oracle(pr), oracle_mod.Oracle(pr)
+    for it in range(2):
+        ra = a.sample_pass(calls, it, n_threads=1)
+        rb = b.sample_pass(calls, it, n_threads=7)
+        assert ra.n_calls == rb.n_calls and ra.w_max == rb.w_max
+        assert abs(ra.integral - rb.integral) <= 1e-15 * abs(ra.integral)
+        assert abs(ra.variance - rb.variance) <= 1e-13 * ra.variance
+        Da, Db = a.get_pass()["D"], b.get_pass()["D"]
+        assert np.abs(Da - Db).max() <= 1e-14 * Da.max()
+        for o in (a, b):
+            o.refine_grids()
+            o.update_alpha()
