@@ -327,10 +327,18 @@ class Vamp:
                 f"{k['ctas_per_sm']}>")
 
     # -- state ---------------------------------------------------------------
-    def get_state(self):
-        e = np.zeros((self.K, self.d, self.n + 1), np.float64)
-        a = np.zeros(self.K, np.float64)
-        s = np.zeros(self.K, np.float64)
+    def get_state(self, out=None):
+        """Grids, α, shifts and w_max (vamp_get_state).  ``out``: optional dict
+        of C-contiguous float64 arrays "edges" [K, d, n+1], "alpha" [K] and
+        "shift" [K] to fill in place (pinned host memory avoids a staging copy)."""
+        shapes = {"edges": (self.K, self.d, self.n + 1), "alpha": (self.K,), "shift": (self.K,)}
+        if out is None:
+            out = {k: np.zeros(v, np.float64) for k, v in shapes.items()}
+        for k, v in shapes.items():
+            arr = out[k]
+            if arr.dtype != np.float64 or arr.shape != v or not arr.flags.c_contiguous:
+                raise ValueError(f"out[{k!r}] must be a C-contiguous float64 array of shape {v}")
+        e, a, s = out["edges"], out["alpha"], out["shift"]
         wm = C.c_double()
         self._check(self.lib.vamp_get_state(self.h, _ptr(e), _ptr(a), _ptr(s), C.byref(wm)))
         return {"edges": e, "alpha": a, "shift": s, "w_max": wm.value}
