@@ -302,7 +302,7 @@ typedef struct vamp_batch vamp_batch;
 
 /* Creates the batch on the current device with its own CUDA stream; cfgs[i]
  * as for vamp_create (all with the same precision).  autotune_tiles = 1: the
- * first iteration times work-item sizes (512, 2048, 8192 calls) and
+ * first iteration times work-item sizes (512, 1024, 2048, 4096, 8192 calls) and
  * shared-memory budgets (112 KB per CTA with two CTAs per SM, or, in the
  * FP32-eval form, 72 KB with three) once and keeps the fastest; 0: 512 calls
  * per item, 112 KB per CTA. */

@@ -169,12 +169,12 @@ vamp_status autotune(vamp_batch* b, const int64_t* n_calls)
     BCK(b, cudaEventCreate(&e0));
     BCK(b, cudaEventCreate(&e1));
     const int budgets[2] = {112, 72};
-    const int64_t mults[3] = {1, 4, 16};
+    const int64_t mults[5] = {1, 2, 4, 8, 16};
     float best = 1e30f;
     int best_budget = 112;
     int64_t best_items = B;
     for (int bi = 0; bi < 2; ++bi) {
-        for (int mi = 0; mi < 3; ++mi) {
+        for (int mi = 0; mi < 5; ++mi) {
             vamp_status st = apply_shape(b, budgets[bi], B * mults[mi]);
             if (st != VAMP_OK) return st;
             float ms = 0.f;
