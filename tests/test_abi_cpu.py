@@ -83,6 +83,34 @@ def test_create_rejects_bad_maps(lib):
     assert _create_status(lib, pr.replace(channels=bad))[0] == V.VAMP_ERR_INVALID_ARG
 
 
+@pytest.mark.parametrize("bad", ["stratified", "negative_count", "null_table", "channel", "partner",
+                                 "axis", "not_perm", "kind"])
+def test_create_rejects_bad_modes(lib, bad):
+    """Pseudo-stratified flag and channel-equivalence tables are validated on
+    the host, before any device work."""
+    pr = P.ring(3, 6)
+    if bad == "stratified":
+        rc, h = _create_status(lib, pr, stratified=2)
+    elif bad == "negative_count":
+        rc, h = _create_status(lib, pr, n_equiv=-1)
+    elif bad == "null_table":
+        rc, h = _create_status(lib, pr.replace(equivalences=None), n_equiv=2)
+    else:
+        row = [0, 1] + list(range(6)) + [0] * 6
+        if bad == "channel":
+            row[0] = 3
+        elif bad == "partner":
+            row[1] = -1
+        elif bad == "axis":
+            row[2] = 6
+        elif bad == "not_perm":
+            row[3] = row[2]
+        else:
+            row[2 + 6] = 4
+        rc, h = _create_status(lib, pr.replace(equivalences=np.array([row], np.int32)))
+    assert rc == V.VAMP_ERR_INVALID_ARG and not h.value
+
+
 def test_create_without_gpu_fails_cleanly(lib):
     import torch
     if torch.cuda.is_available():
@@ -95,6 +123,7 @@ def test_null_arguments(lib):
     h = C.c_void_p()
     assert lib.vamp_create(None, None, C.byref(h)) == V.VAMP_ERR_INVALID_ARG
     assert lib.vamp_sample_pass(None, 10, 0, None) == V.VAMP_ERR_INVALID_ARG
+    assert lib.vamp_sample_pass_async(None, 10, 0, None) == V.VAMP_ERR_INVALID_ARG
     assert lib.vamp_refine_grids(None) == V.VAMP_ERR_INVALID_ARG
     lib.vamp_destroy(None)
 
