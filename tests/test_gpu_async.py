@@ -29,10 +29,10 @@ def _check(dev_row, r, tol):
     assert abs(dev_row[1] - r.variance) <= tol * (r.variance + r.integral ** 2 / r.n_calls)
 
 
-@pytest.mark.parametrize("precision,tol", [(0, 1e-12), (1, 1e-9)])
-def test_async_pass_equals_sync(V, precision, tol):
+@pytest.mark.parametrize("precision,tol,stratified", [(0, 1e-12, 0), (1, 1e-9, 0), (0, 1e-12, 1)])
+def test_async_pass_equals_sync(V, precision, tol, stratified):
     import torch
-    pr = P.bw_gauss()
+    pr = P.bw_gauss().replace(stratified=stratified)
     a = V.Vamp(pr, precision=precision)
     b = V.Vamp(pr, precision=precision)
     out = torch.zeros((4, 9), dtype=torch.float64, device="cuda")
