@@ -130,7 +130,9 @@ vamp::PassArgs pass_args(const vamp_ctx* c, uint32_t field)
 // count (power-of-two class), measured once per process on a pass of the
 // context's first call count and then reused.
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int, int, int, int>, const PassVariant*> g_tuned;
+// key: device, precision, d, n, K (capped), call-count class, pseudo-stratified (whose candidates
+// are the generic kernels only)
+std::map<std::tuple<int, int, int, int, int, int, int>, const PassVariant*> g_tuned;
 
 // Tile and shared memory of one candidate (its CTAs-per-SM budget).
 struct VariantShape {
@@ -183,13 +185,14 @@ vamp_status choose_variant(vamp_ctx* c, int64_t n_calls)
     const int64_t probe = std::min<int64_t>(std::max<int64_t>(n_calls, 1 << 16), 1 << 24);
     int nclass = 0;
     while ((int64_t(1) << (nclass + 1)) <= probe) ++nclass;
-    const auto key = std::make_tuple(c->dev, c->fp32, c->d, c->n, std::min(c->K, 64), nclass);
+    const auto key = std::make_tuple(c->dev, c->fp32, c->d, c->n, std::min(c->K, 64), nclass, c->prm.stratified);
     const PassVariant* best = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tuned.find(key);
         if (it != g_tuned.end()) best = it->second;
     }
+    if (best && std::find(cand.begin(), cand.end(), best) == cand.end()) best = nullptr;  // not a candidate here
     if (!best && cand.size() == 1) best = cand[0];
     if (!best) {
         // time each candidate on a pass of `probe` calls over the current

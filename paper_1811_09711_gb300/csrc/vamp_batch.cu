@@ -55,6 +55,12 @@ struct vamp_batch {
     int64_t fixed_item_calls = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    // pseudo-stratified instances: cell sums per instance, sized by the calls
+    // requested (grown between iterations; the kernels read the pointer from
+    // the device parameter table, so the captured graph stays valid)
+    int strat = 0;
+    std::vector<double*> cellbuf;
+    std::vector<int64_t> cellcap;
     std::string err;
 };
 
@@ -97,6 +103,7 @@ vamp::MultiArgs margs(const vamp_batch* b)
     M.nrows = b->nrows;
     M.max_n = b->max_n;
     M.item_calls = b->item_calls;
+    M.any_strat = b->strat;
     return M;
 }
 
@@ -118,15 +125,42 @@ vamp_status apply_shape(vamp_batch* b, int budget_kb, int64_t item_calls)
     int maxsm = 0;
     BCK(b, cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, b->dev));
     if ((int)smem > maxsm) return bfail(b, VAMP_ERR_INVALID_ARG, "an instance's grid is too large for shared memory");
-    BCK(b, vamp::ensure_smem(vamp::pass_multi_kernel(b->fp32, b->minb), smem));
+    BCK(b, vamp::ensure_smem(vamp::pass_multi_kernel(b->fp32, b->minb, b->strat), smem));
     int bps = 0;
-    BCK(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, vamp::pass_multi_kernel(b->fp32, b->minb), vamp::PASS_THREADS,
+    BCK(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, vamp::pass_multi_kernel(b->fp32, b->minb, b->strat),
+                                                         vamp::PASS_THREADS,
                                                          smem));
     BCK(b, cudaMemcpyAsync(b->d_tiles, b->tiles.data(), b->n * sizeof(int), cudaMemcpyHostToDevice, b->stream));
     b->smem = smem;
     b->grid = (bps > 0 ? bps : 1) * b->sm_count;
     b->budget_kb = budget_kb;
     b->item_calls = item_calls;
+    return VAMP_OK;
+}
+
+// Cell-sum buffers of the pseudo-stratified instances for a pass of n_calls
+// each: at most (N + K n_min) / 2 + K cells (two calls or more per cell).
+vamp_status ensure_cells(vamp_batch* b, const int64_t* n_calls)
+{
+    for (int i = 0; i < b->n; ++i) {
+        Params& P = b->prm[i];
+        if (!P.stratified) continue;
+        const int64_t need = (n_calls[i] + (int64_t)P.K * P.n_min) / 2 + P.K;
+        if (need <= b->cellcap[i]) continue;
+        BCK(b, cudaStreamSynchronize(b->stream));
+        cudaFree(b->cellbuf[i]);
+        b->cellbuf[i] = nullptr;
+        b->cellcap[i] = 0;
+        P.cellsum = nullptr;
+        if (cudaMalloc(&b->cellbuf[i], (size_t)need * 8) != cudaSuccess) {
+            b->cellbuf[i] = nullptr;
+            return bfail(b, VAMP_ERR_OOM, "cell sums of a pseudo-stratified instance");
+        }
+        b->cellcap[i] = need;
+        P.cellsum = b->cellbuf[i];
+        BCK(b, cudaMemcpyAsync(b->d_inst + i, &P, sizeof(Params), cudaMemcpyHostToDevice, b->stream));
+        BCK(b, cudaStreamSynchronize(b->stream));
+    }
     return VAMP_OK;
 }
 
@@ -216,6 +250,7 @@ void vamp_batch_destroy(vamp_batch* b)
     if (prev != b->dev) cudaSetDevice(b->dev);
     if (b->stream) cudaStreamSynchronize(b->stream);
     drop_graph(b);
+    for (double* q : b->cellbuf) cudaFree(q);
     cudaFree(b->arena);
     cudaFreeHost(b->h_it);
     cudaFreeHost(b->h_ncalls);
@@ -238,6 +273,8 @@ vamp_status vamp_batch_create(const vamp_config* cfgs, int32_t n, int32_t autotu
     std::vector<vamp::Setup> setups(n);
     std::vector<vamp::Arena> ars(n);
     b->prm.resize(n);
+    b->cellbuf.assign(n, nullptr);
+    b->cellcap.assign(n, 0);
     b->tiles.assign(n, 1);
     b->combine_from.resize(n);
     b->K.resize(n);
@@ -251,13 +288,14 @@ vamp_status vamp_batch_create(const vamp_config* cfgs, int32_t n, int32_t autotu
     for (int i = 0; i < n; ++i) {
         std::string why;
         Params p{};
-        if (cfgs[i].stratified || !vamp::build_setup(&cfgs[i], p, setups[i], why)) {  // batches: importance sampling
+        if (!vamp::build_setup(&cfgs[i], p, setups[i], why)) {
             delete b;
             return VAMP_ERR_INVALID_ARG;
         }
         if (i == 0) b->fp32 = setups[0].fp32;
         if (setups[i].fp32 != b->fp32) { delete b; return VAMP_ERR_INVALID_ARG; }
         b->prm[i] = p;
+        if (p.stratified) b->strat = 1;
         ars[i] = vamp::plan_arena(p);
         offs[i] = total;
         total += a256(ars[i].bytes);
@@ -368,8 +406,8 @@ vamp_status vamp_batch_iterate(vamp_batch* b, const int64_t* n_calls, uint32_t i
     int prev = -1;
     cudaGetDevice(&prev);
     if (prev != b->dev) cudaSetDevice(b->dev);
-    vamp_status st = VAMP_OK;
-    if (b->tune && !b->tuned) {
+    vamp_status st = ensure_cells(b, n_calls);
+    if (st == VAMP_OK && b->tune && !b->tuned) {
         st = autotune(b, n_calls);
         b->tuned = 1;
         drop_graph(b);

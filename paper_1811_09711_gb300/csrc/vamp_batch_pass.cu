@@ -93,7 +93,9 @@ __device__ __forceinline__ bool run_item(const MultiArgs& M, const Params& P, Sm
             }
             ++u;
         }
-        phase_c_int<T, CPT>(sh, C, sft, Ds, s1, s2, wm, bad);
+        phase_c_int<T, CPT>(sh, C, sft, Ds, s1, s2, wm, bad,
+                            (SH::kStrat && P.stratified) ? CellSums{P.cellsum, base - P.Pc[c], P.spc[c], P.coff[c]}
+                                                         : CellSums{nullptr, 0, 1, 0});
     }
     // uses of each buffer in this item
     if (streaming) {
@@ -108,7 +110,7 @@ __device__ __forceinline__ bool run_item(const MultiArgs& M, const Params& P, Sm
     return true;
 }
 
-template <typename T, int MINB>
+template <typename T, int MINB, bool STRAT>
 __global__ void __launch_bounds__(PASS_THREADS, MINB) k_pass_multi(MultiArgs M)
 {
     static_assert(sizeof(Params) <= PARAMS_SLOT, "Params does not fit its shared-memory slot");
@@ -158,7 +160,10 @@ __global__ void __launch_bounds__(PASS_THREADS, MINB) k_pass_multi(MultiArgs M)
         __syncthreads();
         const int d = Ps.d;
         bool ok;
-        if (d <= 4) ok = run_item<T, 2, Shape<T, 0, 0, 4, 1>>(M, Ps, H, buf0, inst, c, kth, pp, bad);
+        // pseudo-stratified instances: the generic shape, which carries the
+        // cell digits and cell sums (compiled only into the STRAT form)
+        if (STRAT && Ps.stratified) ok = run_item<T, 1, Shape<T, 0, 0>>(M, Ps, H, buf0, inst, c, kth, pp, bad);
+        else if (d <= 4) ok = run_item<T, 2, Shape<T, 0, 0, 4, 1>>(M, Ps, H, buf0, inst, c, kth, pp, bad);
         else if (d <= 8) ok = run_item<T, 2, Shape<T, 0, 0, 8, 5>>(M, Ps, H, buf0, inst, c, kth, pp, bad);
         else if (d <= 12) ok = run_item<T, 1, Shape<T, 0, 0, 12, 9>>(M, Ps, H, buf0, inst, c, kth, pp, bad);
         else ok = run_item<T, 1, Shape<T, 0, 0, 16, 13>>(M, Ps, H, buf0, inst, c, kth, pp, bad);
@@ -172,17 +177,27 @@ __global__ void __launch_bounds__(PASS_THREADS, MINB) k_pass_multi(MultiArgs M)
 }
 
 // Compiled for two or (FP32-eval) three CTAs per SM.
-const void* pass_multi_kernel(int fp32, int minb)
+const void* pass_multi_kernel(int fp32, int minb, int strat)
 {
-    if (!fp32) return (const void*)k_pass_multi<double, 2>;
-    return minb >= 3 ? (const void*)k_pass_multi<float, 3> : (const void*)k_pass_multi<float, 2>;
+    if (strat) {
+        if (!fp32) return (const void*)k_pass_multi<double, 2, true>;
+        return minb >= 3 ? (const void*)k_pass_multi<float, 3, true> : (const void*)k_pass_multi<float, 2, true>;
+    }
+    if (!fp32) return (const void*)k_pass_multi<double, 2, false>;
+    return minb >= 3 ? (const void*)k_pass_multi<float, 3, false> : (const void*)k_pass_multi<float, 2, false>;
 }
 
 cudaError_t launch_pass_multi(int fp32, int minb, const MultiArgs& M, int grid, size_t smem, cudaStream_t s)
 {
-    if (!fp32) k_pass_multi<double, 2><<<grid, PASS_THREADS, smem, s>>>(M);
-    else if (minb >= 3) k_pass_multi<float, 3><<<grid, PASS_THREADS, smem, s>>>(M);
-    else k_pass_multi<float, 2><<<grid, PASS_THREADS, smem, s>>>(M);
+    if (M.any_strat) {
+        if (!fp32) k_pass_multi<double, 2, true><<<grid, PASS_THREADS, smem, s>>>(M);
+        else if (minb >= 3) k_pass_multi<float, 3, true><<<grid, PASS_THREADS, smem, s>>>(M);
+        else k_pass_multi<float, 2, true><<<grid, PASS_THREADS, smem, s>>>(M);
+    } else {
+        if (!fp32) k_pass_multi<double, 2, false><<<grid, PASS_THREADS, smem, s>>>(M);
+        else if (minb >= 3) k_pass_multi<float, 3, false><<<grid, PASS_THREADS, smem, s>>>(M);
+        else k_pass_multi<float, 2, false><<<grid, PASS_THREADS, smem, s>>>(M);
+    }
     return cudaGetLastError();
 }
 

@@ -127,6 +127,7 @@ struct MultiArgs {
     int nrows;
     int max_n;                   // largest bins per axis
     int64_t item_calls;          // calls per work item (multiple of PASS_THREADS*CPT)
+    int any_strat;               // some instance samples pseudo-stratified (its own kernel form)
 };
 constexpr int PARAMS_SLOT = 512;  // bytes reserved for an instance's Params in shared memory
 
@@ -134,7 +135,8 @@ cudaError_t launch_batch_begin(const MultiArgs& M, cudaStream_t s);
 cudaError_t launch_batch_after(const MultiArgs& M, cudaStream_t s);  // finish, refine, α, gather
 // minb: CTAs per SM the kernel is compiled for (2, or 3 in the FP32-eval form)
 cudaError_t launch_pass_multi(int fp32, int minb, const MultiArgs& M, int grid, size_t smem, cudaStream_t s);
-const void* pass_multi_kernel(int fp32, int minb);
+// strat: the form that also runs pseudo-stratified instances
+const void* pass_multi_kernel(int fp32, int minb, int strat = 0);
 
 cudaError_t launch_begin_pass(const Params& P, int64_t N, cudaStream_t s);
 cudaError_t launch_finish_pass(const Params& P, int combine, cudaStream_t s);

@@ -68,11 +68,11 @@ __device__ void begin_pass_dev(const Params& P, int64_t N)
 }
 
 // Stratified passes: Q_c = Σ over the channel's cells of the squared cell
-// sums, one block per channel, fixed-order reduction.
-__global__ void k_strat_q(Params P)
+// sums, one 256-thread block per channel, fixed-order reduction (the same
+// for a context and for an instance of a batch).
+__device__ void strat_q_channel(const Params& P, int c)
 {
     __shared__ double part[256];
-    const int c = blockIdx.x;
     const int64_t a = P.coff[c], b = P.coff[c + 1];
     double s = 0.0;
     for (int64_t q = a + threadIdx.x; q < b; q += blockDim.x) {
@@ -86,6 +86,11 @@ __global__ void k_strat_q(Params P)
         __syncthreads();
     }
     if (threadIdx.x == 0) P.Qc[c] = part[0];
+}
+
+__global__ void k_strat_q(Params P)
+{
+    strat_q_channel(P, blockIdx.x);
 }
 
 __global__ void k_begin_pass(Params P, int64_t N)
@@ -571,6 +576,26 @@ __global__ void k_batch_begin(MultiArgs M)
     const size_t nd = (size_t)P.K * P.d * P.n;
     for (size_t q = threadIdx.x; q < nd; q += blockDim.x) P.D[q] = 0.0;
     for (int q = threadIdx.x; q < 2 * P.K; q += blockDim.x) P.csum[q] = 0.0;
+    if (P.stratified) {
+        // the cells of this pass (first cell of each channel set above)
+        __syncthreads();
+        const int64_t ncell = P.coff[P.K];
+        for (int64_t q = threadIdx.x; q < ncell; q += blockDim.x) P.cellsum[q] = 0.0;
+    }
+}
+
+// Stratified instances: Q_c per (instance, channel) pair, one block each.
+__global__ void k_batch_strat_q(MultiArgs M)
+{
+    const int pair = blockIdx.x;
+    int lo = 0, hi = M.n_inst - 1;  // instance of the pair
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (M.pair_off[mid] <= pair) lo = mid; else hi = mid - 1;
+    }
+    const Params& P = M.inst[lo];
+    if (!P.stratified) return;
+    strat_q_channel(P, pair - M.pair_off[lo]);
 }
 
 // Work items: every (instance, channel) pair with N_c calls gives
@@ -657,8 +682,14 @@ cudaError_t launch_batch_begin(const MultiArgs& M, cudaStream_t s)
 
 cudaError_t launch_batch_after(const MultiArgs& M, cudaStream_t s)
 {
+    cudaError_t e;
+    if (M.any_strat) {
+        k_batch_strat_q<<<M.npairs, 256, 0, s>>>(M);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
     k_batch_finish<<<M.n_inst, 64, 0, s>>>(M);
-    cudaError_t e = cudaGetLastError();
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int blocks = (M.nrows + REFINE_WARPS - 1) / REFINE_WARPS;
     k_batch_refine<<<blocks, REFINE_WARPS * 32, (size_t)REFINE_WARPS * (4 * M.max_n + 2) * sizeof(double), s>>>(M);

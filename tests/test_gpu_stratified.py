@@ -1,8 +1,9 @@
 """Pseudo-stratified sampling in r space (§3.3) on the GPU against the FP64
 oracle: the cells, forward bins and per-call values bit-exact / 1e-12,
 whole adaptation runs (integral, stratified variance, D, edges, α) within
-1e-12 in FP64, the FP32-eval form within its tolerance; batches, servers and
-the allocation-free pass reject the mode."""
+1e-12 in FP64, the FP32-eval form within its tolerance; instances of a batch
+equal the same problems alone and the oracle; servers and the allocation-free
+pass reject the mode."""
 import numpy as np
 import pytest
 
@@ -56,6 +57,20 @@ def test_stratified_calls_bit_exact_fp64(V, O):
             assert rel(r["w"][q], ref["w"]) < 1e-12
 
 
+def test_stratified_context_after_a_tuned_importance_context(V, O):
+    """The kernel choice cached for an importance-sampled context of the same
+    shape and call count is not reused for a pseudo-stratified one (whose
+    candidates are the generic kernels with the cell code)."""
+    pr = P.bw_gauss()
+    V.Vamp(pr, precision=1).sample_pass(50_000, 0)  # tunes (and caches) the shape-specialised kernel
+    g = V.Vamp(pr.replace(stratified=1), precision=1)
+    r = g.sample_pass(50_000, 0)
+    assert g.kernel_info()["shape_d"] == 0
+    ro = O.Oracle(pr.replace(stratified=1)).sample_pass(50_000, 0, n_threads=NTHREADS)
+    assert r.n_calls == ro.n_calls
+    assert abs(r.integral - ro.integral) < 0.05 * np.sqrt(ro.variance)
+
+
 def test_stratified_fp32_eval_accuracy(V, O):
     pr = P.bw_gauss().replace(stratified=1)
     o = O.Oracle(pr)
@@ -74,11 +89,48 @@ def test_stratified_fp32_eval_accuracy(V, O):
     assert rel(rg.variance, ro.variance) < 1e-3
 
 
-def test_batch_server_and_static_reject_stratified(V):
+@pytest.mark.parametrize("precision,tol", [(0, 1e-12), (1, 1e-9)])
+def test_stratified_instances_in_a_batch_equal_alone(V, precision, tol):
+    """Pseudo-stratified and importance-sampled instances in one persistent
+    launch give what each gives alone; the second call count is larger than
+    the first, so the instances' cell-sum buffers grow between iterations."""
+    probs = [P.bw_gauss().replace(stratified=1), P.single_gauss().replace(stratified=1),
+             P.batch_instance(3), P.ring(3, 5).replace(stratified=1)]
+    batch = V.Batch(probs, precision=precision, autotune=False)
+    alone = [V.Vamp(pr, precision=precision) for pr in probs]
+    for it, calls in enumerate((40_000, 40_000, 120_000)):
+        rb = batch.iterate([calls] * len(probs), it, adapt=3)
+        for i, g in enumerate(alone):
+            ra = g.sample_pass(calls, it)
+            g.refine_grids()
+            g.update_alpha()
+            assert rb[i].n_calls == ra.n_calls, (i, it)
+            assert abs(rb[i].integral - ra.integral) <= tol * abs(ra.integral), (i, it)
+            m2 = ra.variance + ra.integral ** 2 / ra.n_calls
+            assert abs(rb[i].variance - ra.variance) <= 10 * tol * m2, (i, it)
+            np.testing.assert_allclose(batch.get_state(i)["edges"], g.get_state()["edges"], rtol=0,
+                                       atol=1e3 * tol)
+
+
+def test_stratified_batch_matches_oracle_fp64(V, O):
+    pr = P.bw_gauss().replace(stratified=1, combine_from=1)
+    batch = V.Batch([pr, P.single_gauss().replace(stratified=1)], precision=0, autotune=False)
+    o = O.Oracle(pr)
+    for it in range(3):
+        rb = batch.iterate([100_000, 20_000], it, adapt=3)
+        ro = o.sample_pass(100_000, it, combine=True, n_threads=NTHREADS)
+        o.refine_grids()
+        o.update_alpha()
+        assert rb[0].n_calls == ro.n_calls
+        assert rel(rb[0].integral, ro.integral) < 1e-12
+        m2 = ro.variance + ro.integral ** 2 / ro.n_calls
+        assert abs(rb[0].variance - ro.variance) <= 1e-12 * m2
+        np.testing.assert_allclose(batch.get_state(0)["edges"], o.get_state()["edges"], rtol=0, atol=1e-12)
+
+
+def test_server_and_static_reject_stratified(V):
     import torch
     pr = P.bw_gauss().replace(stratified=1)
-    with pytest.raises(V.VampError):
-        V.Batch([pr], precision=1)
     srv = V.Server(max_slots=2, precision=1)
     with pytest.raises(V.VampError):
         srv.submit(pr, 2, 10_000)
