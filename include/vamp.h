@@ -119,8 +119,8 @@ typedef struct {
                                    per channel n_r = the largest m (<= 2^20) with 2 m^d <= N_c cells
                                    per axis, s = floor(N_c / n_r^d) calls per cell, N_c = s n_r^d;
                                    the per-call variance is the mean of the cells' sample variances.
-                                   Generation stays importance sampling.  Contexts and batches (the
-                                   request server and the allocation-free pass reject it). */
+                                   Generation stays importance sampling.  Contexts, batches and the
+                                   request server (the allocation-free pass rejects it). */
     int32_t n_equiv;            /* channel equivalences (§3.5), 0..65536; 0 = none */
     const int32_t *equiv;       /* [n_equiv][2 + 2d] host, copied at creation: records
                                    (c, c', π_0..π_{d-1}, kind_0..kind_{d-1}).  Before each

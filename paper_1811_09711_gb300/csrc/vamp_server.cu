@@ -119,6 +119,7 @@ struct vamp_server {
     size_t tick_budget = vamp::TILE_BUDGET;
     size_t tick_smem = 0;
     int tick_grid = 0;
+    int tick_strat = 0;                // kernel form of the cached shape: with the cell code
     cudaEvent_t tick_ev = nullptr;     // end of the launch in flight
     std::vector<Req*> tick_reqs;       // its members
     // multi-instance launch arrays (capacity grows on demand)
@@ -175,9 +176,11 @@ void free_req(vamp_server* s, Req* r)
     delete r;
 }
 
-// Bytes a request needs on the device once admitted: its state arena and the
-// generation staging of its pass kernel (chunks of PASS_THREADS * CPT calls).
-size_t request_bytes(const Req* r, size_t* o_stage, size_t* o_call, size_t* o_cnt, size_t* o_off)
+// Bytes a request needs on the device once admitted: its state arena, the
+// cell sums of a pseudo-stratified request (at most (N + K n_min) / 2 + K
+// cells) and the generation staging of its pass kernel (chunks of
+// PASS_THREADS * CPT calls).
+size_t request_bytes(const Req* r, size_t* o_cells, size_t* o_stage, size_t* o_call, size_t* o_cnt, size_t* o_off)
 {
     const int64_t chunk = (int64_t)vamp::PASS_THREADS * r->var->cpt;
     const int64_t B = r->cfg.gen_batch > 0 ? r->cfg.gen_batch : (int64_t(1) << 20);
@@ -185,6 +188,8 @@ size_t request_bytes(const Req* r, size_t* o_stage, size_t* o_call, size_t* o_cn
     const size_t rec = (size_t)vamp_record_bytes(r->cfg.d);
     const bool gen = r->n_events > 0;
     size_t off = a256(r->ar.bytes);
+    *o_cells = off;
+    if (r->P.stratified) off += a256((size_t)((r->calls + (int64_t)r->P.K * r->P.n_min) / 2 + r->P.K) * 8);
     *o_stage = off;
     off += gen ? a256((size_t)nch * chunk * rec) : 0;
     *o_call = off;
@@ -201,18 +206,19 @@ size_t request_bytes(const Req* r, size_t* o_stage, size_t* o_call, size_t* o_cn
 // integration launches once the recorded event has completed.
 vamp_status admit(vamp_server* s, Req* r)
 {
-    size_t o_stage, o_call, o_cnt, o_off;
+    size_t o_cells, o_stage, o_call, o_cnt, o_off;
     r->lane = take_lane(s);
     if (r->lane < 0) return VAMP_ERR_CUDA;
     r->stream = s->lanes[r->lane].stream;
     r->ev = s->lanes[r->lane].ev;
     r->h_head = reinterpret_cast<Scalars*>(s->h_heads + (size_t)r->lane * s->head_stride);
-    r->bytes = request_bytes(r, &o_stage, &o_call, &o_cnt, &o_off);
+    r->bytes = request_bytes(r, &o_cells, &o_stage, &o_call, &o_cnt, &o_off);
     cudaError_t e = cudaMallocFromPoolAsync(&r->mem, r->bytes, s->pool, r->stream);
     if (e != cudaSuccess) { r->mem = nullptr; r->bytes = 0; return VAMP_ERR_OOM; }
     s->used_mem += (int64_t)r->bytes;
     unsigned char* base = (unsigned char*)r->mem;
     vamp::bind_arena(r->P, base, r->ar);
+    if (r->P.stratified) r->P.cellsum = reinterpret_cast<double*>(base + o_cells);
     r->staging = base + o_stage;
     r->callidx = (uint32_t*)(base + o_call);
     r->counts = (int*)(base + o_cnt);
@@ -312,13 +318,16 @@ vamp_status tick_launch(vamp_server* s, const std::vector<Req*>& ints)
     }
     s->h_it->iteration = 0;
     s->h_it->adapt = 3;
-    if (smem != s->tick_smem) {
-        const void* fn = vamp::pass_multi_kernel(s->fp32, s->tick_minb);
+    int strat = 0;
+    for (Req* r : ints) strat |= r->P.stratified;
+    if (smem != s->tick_smem || strat != s->tick_strat) {
+        const void* fn = vamp::pass_multi_kernel(s->fp32, s->tick_minb, strat);
         int bps = 0;
         if (vamp::ensure_smem(fn, smem) != cudaSuccess ||
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, vamp::PASS_THREADS, smem) != cudaSuccess)
             return VAMP_ERR_CUDA;
         s->tick_smem = smem;
+        s->tick_strat = strat;
         s->tick_grid = (bps > 0 ? bps : 1) * s->sm_count;
     }
     cudaStream_t st0 = s->stream;
@@ -347,6 +356,7 @@ vamp_status tick_launch(vamp_server* s, const std::vector<Req*>& ints)
     M.nrows = s->h_row_off[n];
     M.max_n = max_n;
     M.item_calls = (int64_t)vamp::PASS_THREADS * 8;
+    M.any_strat = strat;
     if (e == cudaSuccess) e = vamp::launch_batch_begin(M, st0);
     if (e == cudaSuccess) e = vamp::launch_pass_multi(s->fp32, s->tick_minb, M, s->tick_grid, smem, st0);
     if (e == cudaSuccess) e = vamp::launch_batch_after(M, st0);
@@ -452,8 +462,8 @@ void scheduler(vamp_server* s)
             int64_t pending = 0;
             while (!s->queue.empty() && (int)(s->active.size() + admitted.size()) < s->max_slots) {
                 Req* r = s->queue.front();
-                size_t a, b2, c, dd;
-                const int64_t need = (int64_t)request_bytes(r, &a, &b2, &c, &dd);
+                size_t a0, a, b2, c, dd;
+                const int64_t need = (int64_t)request_bytes(r, &a0, &a, &b2, &c, &dd);
                 if (s->used_mem + pending + need > s->budget && !(s->active.empty() && admitted.empty())) break;
                 s->queue.pop_front();
                 admitted.push_back(r);
@@ -615,7 +625,7 @@ vamp_status vamp_server_submit(vamp_server* s, const vamp_config* cfg, int32_t i
     r->cfg.peaks = r->pk.data();
     r->cfg.peak_weight = r->w.data();
     std::string why;
-    if (cfg->stratified || !vamp::build_setup(&r->cfg, r->P, r->S, why)) {  // requests: importance sampling
+    if (!vamp::build_setup(&r->cfg, r->P, r->S, why)) {
         delete r;
         return VAMP_ERR_INVALID_ARG;
     }

@@ -2,8 +2,8 @@
 oracle: the cells, forward bins and per-call values bit-exact / 1e-12,
 whole adaptation runs (integral, stratified variance, D, edges, α) within
 1e-12 in FP64, the FP32-eval form within its tolerance; instances of a batch
-equal the same problems alone and the oracle; servers and the allocation-free
-pass reject the mode."""
+and requests of a server equal the same problems alone (and the oracle); the
+allocation-free pass rejects the mode."""
 import numpy as np
 import pytest
 
@@ -128,13 +128,36 @@ def test_stratified_batch_matches_oracle_fp64(V, O):
         np.testing.assert_allclose(batch.get_state(0)["edges"], o.get_state()["edges"], rtol=0, atol=1e-12)
 
 
-def test_server_and_static_reject_stratified(V):
+@pytest.mark.parametrize("precision,tol", [(0, 1e-12), (1, 1e-9)])
+def test_stratified_requests_in_a_server_equal_alone(V, precision, tol):
+    """Pseudo-stratified requests served in a mix with an importance-sampled
+    one give what each gives alone."""
+    import torch
+    reqs = [(P.bw_gauss().replace(stratified=1, combine_from=1), 3, 60_000),
+            (P.batch_instance(7), 2, 30_000),
+            (P.single_gauss().replace(stratified=1, combine_from=1), 4, 20_000)]
+    srv = V.Server(max_slots=4, precision=precision)
+    ids = [srv.submit(pr, iters, calls, 0, 0) for pr, iters, calls in reqs]
+    srv.wait_idle(300.0)
+    done = {r.id: r for r in srv.poll(8)}
+    srv.close()
+    for rid, (pr, iters, calls) in zip(ids, reqs):
+        g = V.Vamp(pr, precision=precision)
+        for it in range(iters):
+            ra = g.sample_pass(calls, it)
+            g.refine_grids()
+            g.update_alpha()
+        torch.cuda.synchronize()
+        r = done[rid]
+        assert r.status == V.VAMP_OK and r.result.n_calls == ra.n_calls
+        assert abs(r.result.integral - ra.integral) <= tol * abs(ra.integral), pr.name
+        m2 = ra.variance + ra.integral ** 2 / ra.n_calls
+        assert abs(r.result.variance - ra.variance) <= 10 * tol * m2, pr.name
+
+
+def test_static_pass_rejects_stratified(V):
     import torch
     pr = P.bw_gauss().replace(stratified=1)
-    srv = V.Server(max_slots=2, precision=1)
-    with pytest.raises(V.VampError):
-        srv.submit(pr, 2, 10_000)
-    srv.close()
     st = V.Vamp(pr.replace(stratified=0)).get_state()
     e = torch.tensor(st["edges"], dtype=torch.float64, device="cuda")
     a = torch.tensor(st["alpha"], dtype=torch.float64, device="cuda")
