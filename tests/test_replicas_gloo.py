@@ -60,3 +60,17 @@ def test_two_replicas_over_gloo(oracle_mod):
 def test_single_rank_is_identity():
     import bench
     assert bench.job_throughput(12.5, 7.0, 1) == (12.5, 7.0)
+
+
+def test_roofline_operation_counts():
+    """The per-call operation count charged to the roofline, term by term:
+    8 per lookup x K d, 15 per mapped coordinate, 7 per channel, 8 per
+    coordinate, 60 per Philox block, 10 for the weight and sums."""
+    import bench
+    from paper_1811_09711_gb300 import problems as P
+    pr = P.collider()
+    K, d = pr.n_channels, pr.d
+    mapped = int(pr.channels.n_mapped.sum())
+    assert (K, d, mapped) == (64, 14, 188)
+    assert bench.lookup_ops_per_call(pr) == 8 * K * d == 7168
+    assert bench.algorithmic_ops_per_call(pr) == 8 * K * d + 15 * mapped + 7 * K + 8 * d + 60 * 4 + 10 == 10798
