@@ -158,8 +158,10 @@ typedef struct vamp_ctx vamp_ctx;
  * descriptor), OOM, CUDA.  *out is NULL on failure. */
 vamp_status vamp_create(const vamp_config *cfg, void *cuda_stream, vamp_ctx **out);
 
-/* One importance-sampling pass with the current grids and α (§3.5 work
- * order): N_c = max(n_min, floor(α_c n_calls)) calls per live channel; each
+/* One sampling pass with the current grids and α (§3.5 work order; by
+ * importance, or pseudo-stratified in r space when cfg->stratified is set,
+ * §3.3): N_c = max(n_min, floor(α_c n_calls)) calls per live channel (whole
+ * cells of that size when stratified); each
  * call maps r -> x_c -> p, evaluates f, inverts every other channel for g(p),
  * and accumulates w = f/g into per-channel sums, the bin d-values
  * D_{c,k,j} = Σ w^2 (Eq. 15) and the maximum weight.  `iteration` (< 2^31)
