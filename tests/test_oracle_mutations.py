@@ -63,6 +63,13 @@ MUTATIONS = [
      "double tgt = (1.0 - u) * A[o->K - 1];", "channel_choice_is_inverse_cdf"),
     ("accept_inverted", "if (unif(X[d + 1]) * wm < fabs(w)) {", "if (unif(X[d + 1]) * wm > fabs(w)) {",
      "generation_brute_force"),
+    ("alloc_threshold_dropped", "if (nc < n_min) nc = n_min;", "if (nc < 0) nc = n_min;", "test_allocation"),
+    ("alloc_rounded", "nc = (int64_t)floor(alpha[c] * (double)N);", "nc = (int64_t)llround(alpha[c] * (double)N);",
+     "test_allocation"),
+    ("combination_unweighted", "ks_add(&swi, o->hist_I[h] / o->hist_V[h]);", "ks_add(&swi, o->hist_I[h] / o->hist_V[h] * o->hist_V[h]);",
+     "combination_inverse_variance"),
+    ("chi2_dof_off_by_one", "o->comb_chi2 = ks_val(&chi) / (double)(cnt - 1);", "o->comb_chi2 = ks_val(&chi) / (double)cnt;",
+     "combination_inverse_variance"),
     # pseudo-stratified mode (R16, R17): pins in test_oracle_stratified.py
     ("strat_variance_no_bessel", "V = (ks_val(&s2) - ks_val(&qq) / s) / ((double)o->Cc[c] * (s - 1.0));",
      "V = (ks_val(&s2) - ks_val(&qq) / s) / ((double)o->Cc[c] * s);",

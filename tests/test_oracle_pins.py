@@ -486,6 +486,8 @@ def test_allocation(oracle_mod):
     assert list(nc) == [999, 10]
     nc, _ = oracle_mod.allocate([1 / 3] * 3, 100)
     assert list(nc) == [33, 33, 33]
+    nc, _ = oracle_mod.allocate([0.6666, 0.3334], 1000)  # floor, not rounding (R6)
+    assert list(nc) == [666, 333]
 
 
 def test_alpha_update_properties(oracle_mod):
