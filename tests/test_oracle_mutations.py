@@ -70,6 +70,12 @@ MUTATIONS = [
      "combination_inverse_variance"),
     ("chi2_dof_off_by_one", "o->comb_chi2 = ks_val(&chi) / (double)(cnt - 1);", "o->comb_chi2 = ks_val(&chi) / (double)cnt;",
      "combination_inverse_variance"),
+    ("rebin_zero_weight_limit", "if (r == 0.0) mj = 0.0;                    /* R2 */",
+     "if (r == 0.0) mj = 1.0;                    /* R2 */", "refine"),
+    ("alpha_zero_channel_kept", "else if (Ic[c] == 0.0) a = 0.0; /* all calls gave w = 0: switch off */",
+     "else if (Ic[c] == 0.0) a = alpha[c];", "alpha_update_properties"),
+    ("wmax_not_raised_between_batches", "        if (bmax > o->wmax) o->wmax = bmax;\n        ++b;",
+     "        ++b;", "generation_brute_force"),
     # pseudo-stratified mode (R16, R17): pins in test_oracle_stratified.py
     ("strat_variance_no_bessel", "V = (ks_val(&s2) - ks_val(&qq) / s) / ((double)o->Cc[c] * (s - 1.0));",
      "V = (ks_val(&s2) - ks_val(&qq) / s) / ((double)o->Cc[c] * s);",
