@@ -70,6 +70,8 @@ MUTATIONS = [
      "combination_inverse_variance"),
     ("chi2_dof_off_by_one", "o->comb_chi2 = ks_val(&chi) / (double)(cnt - 1);", "o->comb_chi2 = ks_val(&chi) / (double)cnt;",
      "combination_inverse_variance"),
+    ("bin_rule_strict", "        if (e[mid] <= x) lo = mid; else hi = mid - 1;", "        if (e[mid] < x) lo = mid; else hi = mid - 1;",
+     "bin_rule_at_edges"),
     ("rebin_zero_weight_limit", "if (r == 0.0) mj = 0.0;                    /* R2 */",
      "if (r == 0.0) mj = 1.0;                    /* R2 */", "refine"),
     ("alpha_zero_channel_kept", "else if (Ic[c] == 0.0) a = 0.0; /* all calls gave w = 0: switch off */",

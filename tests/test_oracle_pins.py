@@ -654,3 +654,19 @@ def test_thread_split_is_exact(oracle_mod, factory, calls):
         for o in (a, b):
             o.refine_grids()
             o.update_alpha()
+
+
+def test_bin_rule_at_edges(oracle_mod):
+    """R11: x in bin j iff ξ_j <= x < ξ_{j+1}; a point on an interior edge
+    belongs to the upper bin, x = 1 to the last bin (density 1/(n Δx_j),
+    Eq. 12)."""
+    pr = P.special_case("const", d=1, n_bins=5)
+    o = oracle_mod.Oracle(pr)
+    e = np.array([0.0, 0.1, 0.25, 0.6, 0.7, 1.0])
+    o.set_state(e.reshape(1, 1, 6), np.ones(1), np.zeros(1), 0.0, have_pass=True)
+    dens = 1.0 / (5 * np.diff(e))
+    for j in range(1, 5):
+        assert o.grid_density(0, [e[j]]) == dens[j]
+        assert o.grid_density(0, [np.nextafter(e[j], 0.0)]) == dens[j - 1]
+    assert o.grid_density(0, [1.0]) == dens[4]
+    assert o.grid_density(0, [0.0]) == dens[0]
