@@ -70,6 +70,9 @@ MUTATIONS = [
      "combination_inverse_variance"),
     ("chi2_dof_off_by_one", "o->comb_chi2 = ks_val(&chi) / (double)(cnt - 1);", "o->comb_chi2 = ks_val(&chi) / (double)cnt;",
      "combination_inverse_variance"),
+    ("power_clamp_dropped", "            if (pk < DBL_MIN) pk = DBL_MIN; /* R15 */", "", "clamp_at_zero"),
+    ("smoothing_end_weight", "        t[0] = (Din[0] + Din[1]) / 2.0;", "        t[0] = (Din[0] + Din[1]) / 3.0;",
+     "three_point"),
     ("bin_rule_strict", "        if (e[mid] <= x) lo = mid; else hi = mid - 1;", "        if (e[mid] < x) lo = mid; else hi = mid - 1;",
      "bin_rule_at_edges"),
     ("rebin_zero_weight_limit", "if (r == 0.0) mj = 0.0;                    /* R2 */",

@@ -670,3 +670,35 @@ def test_bin_rule_at_edges(oracle_mod):
         assert o.grid_density(0, [np.nextafter(e[j], 0.0)]) == dens[j - 1]
     assert o.grid_density(0, [1.0]) == dens[4]
     assert o.grid_density(0, [0.0]) == dens[0]
+
+
+def test_power_map_clamp_at_zero(oracle_mod):
+    """R15: where x^5 underflows (or x = 0) the power map gives p = the
+    smallest normal double, not 0, so that the integrand factor and the
+    other channels' inverse maps stay finite; above that p = x^5."""
+    o = oracle_mod.Oracle(P.special_case("pow", d=2))
+    tiny = np.finfo(np.float64).tiny
+    p, _ = o.channel_forward(0, [0.0, 0.5])
+    assert p[0] == tiny and p[1] == 0.5
+    p, jac = o.channel_forward(0, [1e-70, 0.5])  # (1e-70)^5 underflows
+    assert p[0] == tiny and np.isfinite(jac) and jac > 0.0
+    assert np.isfinite(o.f(p)) and np.isfinite(o.g(p))
+    p, _ = o.channel_forward(0, [0.5, 0.5])
+    assert p[0] == 0.5 ** 5
+
+
+def test_smoothing_is_the_three_point_average(oracle_mod):
+    """R3: smooth = 1 rebins from (D_1 + D_2)/2, (D_{j-1} + D_j + D_{j+1})/3,
+    (D_{n-1} + D_n)/2 -- the same edges as rebinning the averaged row."""
+    rng = np.random.default_rng(4)
+    n = 12
+    e = np.sort(np.concatenate([[0, 1], rng.uniform(0, 1, n - 1)]))
+    D = rng.exponential(1.0, n)
+    avg = np.empty(n)
+    avg[0] = (D[0] + D[1]) / 2
+    avg[-1] = (D[-2] + D[-1]) / 2
+    avg[1:-1] = (D[:-2] + D[1:-1] + D[2:]) / 3
+    got = oracle_mod.refine_row(D, e, alpha_grid=1.5, smooth=1)
+    ref = oracle_mod.refine_row(avg, e, alpha_grid=1.5, smooth=0)
+    np.testing.assert_allclose(got, ref, rtol=0, atol=1e-15)
+    assert np.abs(got - oracle_mod.refine_row(D, e, alpha_grid=1.5, smooth=0)).max() > 1e-4
