@@ -1,12 +1,17 @@
 // vamp_kernels.cu -- the small kernels around the pass kernel (vamp_pass.cuh):
 //
-//   k_begin_pass      integer call allocation N_c, prefix P_c (§3.4)
+//   k_begin_pass      integer call allocation N_c, prefix P_c (§3.4); cells of a
+//                     pseudo-stratified pass (§3.3)
+//   k_strat_q         Σ over a channel's cells of the squared cell sums (§3.3)
 //   k_finish_pass     per-channel means/variances, pass result, combination
-//   k_refine          VEGAS rebinning of every (channel, axis) row (Eqs. 14, 15)
+//   k_pass_result     pass result into a caller's device array (asynchronous pass)
+//   k_refine          VEGAS rebinning of every (channel, axis) row (Eqs. 14, 15),
+//                     with the channel equivalences pooled in (§3.5)
 //   k_update_alpha    channel-weight update (Eq. 25)
 //   k_derive          lookup-block rows: densities 1/(n Δx), cell tables, FP32 copies
 //   k_gen_prepare / k_gen_scan / k_gen_copy / k_gen_end   generation bookkeeping
 //   k_eval<T>         per-call diagnostics for parity tests
+//   k_batch_*         the same steps for every instance of a batch or server tick
 #include "vamp_device.cuh"
 #include "vamp_internal.h"
 
