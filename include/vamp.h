@@ -109,7 +109,7 @@ typedef struct {
     uint32_t request_id;        /* Philox counter word 3 */
     double grid_alpha;          /* power α of the rebinning measure (Eq. 14), e.g. 1.5 */
     double beta;                /* power β of the channel-weight update (Eq. 25), e.g. 0.5 */
-    int64_t n_min;              /* lower threshold of calls per live channel, e.g. 10 */
+    int64_t n_min;              /* lower threshold of calls per live channel, e.g. 10 (1..2^32-1) */
     int32_t smooth;             /* 1: 3-point average of the bin d-values before Eq. 14 */
     int32_t omega_mode;         /* ω_c of Eq. 25: 0 = channel variance V_c, 1 = second moment */
     int64_t gen_batch;          /* calls per generation batch (0 = 2^20), <= 2^24 */
@@ -288,6 +288,26 @@ vamp_status vamp_kernel_stats(vamp_ctx *ctx, double *sample_ms, int64_t *sample_
 vamp_status vamp_pass_kernel_info(const vamp_ctx *ctx, int32_t *fp32, int32_t *calls_per_thread,
                                   int32_t *shape_d, int32_t *shape_n, int32_t *ctas_per_sm);
 
+/* Name of the pass kernel the context uses for mode 0 (integration) or 1
+ * (generation), as profilers print it, e.g. "k_pass<float, 0, 2, 14, 100, 2>",
+ * written NUL-terminated into buf (len bytes, host).  INVALID_ARG for a bad
+ * mode or a buffer too small. */
+vamp_status vamp_pass_kernel_name(const vamp_ctx *ctx, int32_t mode, char *buf, int32_t len);
+
+/* Number of compiled pass-kernel variants that can run this context's shape
+ * and sampling mode: the autotuner's candidates, in a fixed order
+ * (shape-specialised kernels first, then the generic ones). */
+vamp_status vamp_pass_kernel_candidates(const vamp_ctx *ctx, int32_t *count);
+
+/* Pins the context's pass kernels (integration and generation) to candidate
+ * `index` (0 <= index < count of vamp_pass_kernel_candidates) instead of the
+ * autotuner's pick at the first pass -- for tests that must run a given
+ * variant and for reproducible timing.  Every candidate computes the same
+ * pass; sums may differ in the order of floating-point additions.  The
+ * choice holds until the context is destroyed.  INVALID_ARG for a bad index;
+ * CUDA if the kernel's shared memory cannot be configured. */
+vamp_status vamp_select_pass_kernel(vamp_ctx *ctx, int32_t index);
+
 /* ---- many independent integrations in one launch --------------------------
  * A batch advances n integrations of possibly different d, K, n, calls and
  * seeds together (all in the same precision): every iteration runs ONE
@@ -375,6 +395,18 @@ vamp_status vamp_server_create(int32_t max_slots, int64_t mem_budget_bytes, int3
 vamp_status vamp_server_submit(vamp_server *s, const vamp_config *cfg, int32_t iterations, int64_t calls,
                                int64_t n_events, int64_t max_gen_calls, void *dev_records, uint64_t *id_out);
 
+/* vamp_server_submit that also hands back the adapted state (the analogue of
+ * the paper's grid files, §4.5): dev_state (device, 8-byte aligned, owned by
+ * the caller and left untouched by anything but this request until its
+ * result is polled; NULL = none) receives, once the last adaptation
+ * iteration is done, the grids [K][d][n+1], α [K] and the channel shifts
+ * [K] (FP64, K*d*(n+1) + 2K doubles) -- what vamp_get_state returns for the
+ * same request run alone.  The copy is complete when the request's result
+ * is polled. */
+vamp_status vamp_server_submit_state(vamp_server *s, const vamp_config *cfg, int32_t iterations, int64_t calls,
+                                     int64_t n_events, int64_t max_gen_calls, void *dev_records, double *dev_state,
+                                     uint64_t *id_out);
+
 /* Moves up to max_results completed requests (completion order) into out
  * (host); returns how many. */
 int32_t vamp_server_poll(vamp_server *s, vamp_request_result *out, int32_t max_results);
@@ -396,10 +428,11 @@ vamp_status vamp_server_load(const vamp_server *s, int32_t *queued, int32_t *int
  * unfinished) and frees everything. */
 void vamp_server_destroy(vamp_server *s);
 
-/* One sampling pass that allocates nothing, for callers that cannot let a
- * library allocate memory (all device memory owned by the caller's own pool,
- * or a path where an allocation could block or fail unpredictably).  The
- * paper has no counterpart: it is an interface addition of this library.
+/* One sampling pass that makes no device-memory allocation, for callers that
+ * cannot let a library allocate device memory (all of it owned by the
+ * caller's own pool, or a path where an allocation could block or fail
+ * unpredictably).  The paper has no counterpart: it is an interface addition
+ * of this library.  (Host-side set-up uses small temporary heap buffers.)
  *
  * Same pass as vamp_sample_pass, without a context: the caller passes the
  * problem (cfg, host memory, read during the call), the grid state in device
@@ -410,12 +443,16 @@ void vamp_server_destroy(vamp_server *s);
  * err_len bytes) receives a message on failure.
  *
  * All working arrays live in one static device array of 8 MiB that every
- * GPU loading this library holds until the process exits; a problem that
- * needs more (about K * d * (n+1) * 32 bytes plus small terms) is rejected
- * with VAMP_ERR_INVALID_ARG and a message.  The call clears what must start
- * at zero; calls that overlap on the GPU share the array and race.  The
- * first call on a device looks up the array's device address (make it
- * before any stream capture).  Synchronises cuda_stream. */
+ * GPU loading this library's device code holds until the process exits; a
+ * problem that needs more (about K * d * (n+1) * 32 bytes plus small terms)
+ * is rejected with VAMP_ERR_INVALID_ARG and a message.  Under CUDA's default
+ * lazy module loading the array comes into being with the module at the
+ * first call on a device (at module load otherwise): make that first call
+ * before a pool of yours reserves all free device memory, and before any
+ * stream capture.  The array's address is looked up on every call in the
+ * current context, so it stays right after a device reset.  The call clears
+ * what must start at zero; calls that overlap on the GPU share the array and
+ * race.  Synchronises cuda_stream. */
 vamp_status vamp_sample_pass_static(const vamp_config *cfg, const double *dev_edges, const double *dev_alpha,
                                     const double *dev_shift, int64_t n_calls, uint32_t iteration,
                                     void *cuda_stream, double *dev_D_out, vamp_pass_result *out,
@@ -429,6 +466,12 @@ const char *vamp_last_error(const vamp_ctx *ctx);
 
 /* Static name of a status code. */
 const char *vamp_status_string(vamp_status s);
+
+/* SHA-256 (hex) of the sources, headers and compiler flags this library was
+ * built from (static string; "unknown" for a build outside the in-tree build
+ * script).  Lets a caller check that the binary is the one its sources
+ * describe. */
+const char *vamp_source_hash(void);
 
 #ifdef __cplusplus
 }

@@ -255,6 +255,11 @@ const char* vamp_status_string(vamp_status s)
 
 const char* vamp_last_error(const vamp_ctx* c) { return c ? c->err.c_str() : ""; }
 
+#ifndef VAMP_SOURCE_HASH
+#define VAMP_SOURCE_HASH "unknown"
+#endif
+const char* vamp_source_hash(void) { return VAMP_SOURCE_HASH; }
+
 int64_t vamp_record_bytes(int32_t d) { return ((4 * (int64_t)d + 7) & ~int64_t(7)) + 8; }
 
 void vamp_destroy(vamp_ctx* c)
@@ -347,7 +352,7 @@ create_fail:
 vamp_status vamp_allocate(vamp_ctx* c, int64_t n_calls, int64_t* n_total)
 {
     if (!c || n_calls < 1) return fail(c, VAMP_ERR_INVALID_ARG, "n_calls must be >= 1");
-    if (n_calls + (int64_t)c->K * c->prm.n_min > int64_t(0xffffffff))
+    if (n_calls > int64_t(0xffffffff) || n_calls > int64_t(0xffffffff) - (int64_t)c->K * c->prm.n_min)
         return fail(c, VAMP_ERR_INVALID_ARG, "too many calls for a 32-bit call counter");
     DeviceGuard g(c->dev);
     VAMP_CK(c, vamp::launch_begin_pass(c->prm, n_calls, c->stream));
@@ -365,7 +370,7 @@ vamp_status enqueue_pass(vamp_ctx* c, int64_t n_calls, uint32_t iteration, cudaE
 {
     if (n_calls < 1) return fail(c, VAMP_ERR_INVALID_ARG, "n_calls must be >= 1");
     if (iteration >= 0x80000000u) return fail(c, VAMP_ERR_INVALID_ARG, "iteration must be < 2^31");
-    if (n_calls + (int64_t)c->K * c->prm.n_min > int64_t(0xffffffff))
+    if (n_calls > int64_t(0xffffffff) || n_calls > int64_t(0xffffffff) - (int64_t)c->K * c->prm.n_min)
         return fail(c, VAMP_ERR_INVALID_ARG, "too many calls for a 32-bit call counter");
     DeviceGuard g(c->dev);
     // stratified passes: cell sums for at most (N + K n_min) / 2 cells (two
@@ -792,6 +797,34 @@ vamp_status vamp_pass_kernel_info(const vamp_ctx* c, int32_t* fp32, int32_t* cpt
     if (shape_d) *shape_d = c->var->D;
     if (shape_n) *shape_n = c->var->NB;
     if (ctas_per_sm) *ctas_per_sm = c->var->minb;
+    return VAMP_OK;
+}
+
+vamp_status vamp_pass_kernel_name(const vamp_ctx* c, int32_t mode, char* buf, int32_t len)
+{
+    if (!c || !c->var || (mode != 0 && mode != 1) || !buf || len < 1) return VAMP_ERR_INVALID_ARG;
+    const vamp::PassVariant* v = c->var;
+    const int k = std::snprintf(buf, (size_t)len, "%s<%s, %d, %d, %d, %d, %d>", v->family,
+                                v->fp32 ? "float" : "double", mode, v->cpt, v->D, v->NB, v->minb);
+    return (k < 0 || k >= len) ? VAMP_ERR_INVALID_ARG : VAMP_OK;
+}
+
+vamp_status vamp_pass_kernel_candidates(const vamp_ctx* c, int32_t* count)
+{
+    if (!c || !count) return VAMP_ERR_INVALID_ARG;
+    *count = (int32_t)vamp::pass_candidates(c->fp32, c->d, c->n, c->prm.stratified).size();
+    return VAMP_OK;
+}
+
+vamp_status vamp_select_pass_kernel(vamp_ctx* c, int32_t index)
+{
+    if (!c) return VAMP_ERR_INVALID_ARG;
+    const std::vector<const PassVariant*> cand = vamp::pass_candidates(c->fp32, c->d, c->n, c->prm.stratified);
+    if (index < 0 || index >= (int32_t)cand.size()) return fail(c, VAMP_ERR_INVALID_ARG, "no such pass-kernel candidate");
+    DeviceGuard g(c->dev);
+    const vamp_status s = use_variant(c, cand[index]);
+    if (s != VAMP_OK) return s;
+    c->tuned = 1;  // the autotuner leaves a pinned choice alone
     return VAMP_OK;
 }
 

@@ -401,7 +401,8 @@ vamp_status vamp_batch_iterate(vamp_batch* b, const int64_t* n_calls, uint32_t i
     if (!n_calls || !results) return bfail(b, VAMP_ERR_INVALID_ARG, "n_calls and results are required");
     if (iteration >= 0x80000000u) return bfail(b, VAMP_ERR_INVALID_ARG, "iteration must be < 2^31");
     for (int i = 0; i < b->n; ++i)
-        if (n_calls[i] < 1 || n_calls[i] + (int64_t)b->K[i] * b->prm[i].n_min > int64_t(0xffffffff))
+        if (n_calls[i] < 1 || n_calls[i] > int64_t(0xffffffff) ||
+            n_calls[i] > int64_t(0xffffffff) - (int64_t)b->K[i] * b->prm[i].n_min)
             return bfail(b, VAMP_ERR_INVALID_ARG, "calls per instance must be >= 1 and < 2^32");
     int prev = -1;
     cudaGetDevice(&prev);

@@ -55,6 +55,7 @@ struct EvalArgs {
 struct PassVariant {
     int fp32, cpt, D, NB;
     int minb;  // CTAs per SM the kernel is compiled for (register cap), sizes its tile budget
+    const char* family;  // kernel template name ("k_pass")
     const void* fn[2];
     cudaError_t (*launch)(const Params& P, int mode, const PassArgs& A, int grid, size_t smem, cudaStream_t s);
 };

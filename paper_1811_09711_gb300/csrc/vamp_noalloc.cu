@@ -1,5 +1,5 @@
-// vamp_noalloc.cu -- vamp_sample_pass_static: one sampling pass without any
-// device or host allocation by the library.
+// vamp_noalloc.cu -- vamp_sample_pass_static: one sampling pass that makes
+// no device-memory allocation.
 //
 // Some callers cannot let a library call cudaMalloc: code that runs inside a
 // framework which owns every byte of device memory through its own pool
@@ -9,21 +9,27 @@
 // the caller passes the grid state and the output buffers, and every
 // working array of the pass (lookup blocks, map records, call allocation,
 // accumulators, scalars) lives in one statically sized device array that
-// the library's image carries.  Every GPU that loads the library holds that
-// array (VAMP_STATIC_SCRATCH_BYTES) until the process exits.
+// the library's image carries.  Every GPU that loads the library's device
+// code holds that array (VAMP_STATIC_SCRATCH_BYTES) until the process exits.
+// With CUDA's default lazy module loading the array (with the module image)
+// comes into being at the first call on a device, otherwise when the module
+// loads: a caller whose pool reserves all free device memory makes that
+// first call before reserving.  Host-side set-up uses small temporary heap
+// buffers for the problem description; no device memory is allocated.
 //
 // The array is shared by all calls: each call clears the parts that must
 // start at zero, and calls that overlap on the GPU (two streams, two host
-// threads) race on it.  The device address of the array is looked up once
-// per device, by the first call made with that device current; make that
-// first call before any stream capture.
+// threads) race on it.  Its device address is looked up on every call with
+// the caller's device current (cudaGetSymbolAddress), so a device reset or
+// another current context never leaves a stale address behind; the first
+// lookup on a device loads the module, so make the first call before any
+// stream capture.
 #include "../../include/vamp.h"
 #include "vamp_device.cuh"
 #include "vamp_internal.h"
 
 #include <cstdio>
 #include <cstring>
-#include <mutex>
 #include <string>
 #include <vector>
 
@@ -33,12 +39,8 @@ using vamp::Scalars;
 namespace {
 
 constexpr size_t VAMP_STATIC_SCRATCH_BYTES = size_t(8) << 20;  // 8 MiB
-constexpr int MAX_DEVICES = 128;
 
 __device__ __align__(256) unsigned char g_scratch[VAMP_STATIC_SCRATCH_BYTES];
-
-std::mutex g_mu;
-void* g_scratch_ptr[MAX_DEVICES] = {};
 
 void put_msg(char* buf, int32_t len, const char* msg)
 {
@@ -47,18 +49,16 @@ void put_msg(char* buf, int32_t len, const char* msg)
     }
 }
 
-// Device address of the scratch array on the current device (looked up once).
-cudaError_t scratch_ptr(int dev, unsigned char** out)
+// Device address of the scratch array in the current context.  Looked up on
+// every call (a table lookup once the module is loaded): an address cached
+// per device ordinal would go stale after cudaDeviceReset or under another
+// current context, where the module and its array are loaded anew.
+cudaError_t scratch_ptr(unsigned char** out)
 {
-    std::lock_guard<std::mutex> lk(g_mu);
-    if (dev < 0 || dev >= MAX_DEVICES) return cudaErrorInvalidDevice;
-    if (!g_scratch_ptr[dev]) {
-        void* p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
-        if (e != cudaSuccess) return e;
-        g_scratch_ptr[dev] = p;
-    }
-    *out = (unsigned char*)g_scratch_ptr[dev];
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+    if (e != cudaSuccess) return e;
+    *out = (unsigned char*)p;
     return cudaSuccess;
 }
 
@@ -87,7 +87,9 @@ extern "C" vamp_status vamp_sample_pass_static(const vamp_config* cfg, const dou
         return VAMP_ERR_INVALID_ARG;
     }
     const int d = S.d, K = S.K, n = S.n;
-    if (n_calls < 1 || iteration >= 0x80000000u || n_calls + (int64_t)K * cfg->n_min > int64_t(0xffffffff)) {
+    // bound n_calls before adding the per-channel minimum (no signed overflow)
+    if (n_calls < 1 || iteration >= 0x80000000u || n_calls > int64_t(0xffffffff) ||
+        n_calls > int64_t(0xffffffff) - (int64_t)K * cfg->n_min) {
         put_msg(err_msg, err_len, "n_calls must be >= 1, iteration < 2^31, total calls < 2^32");
         return VAMP_ERR_INVALID_ARG;
     }
@@ -109,7 +111,7 @@ extern "C" vamp_status vamp_sample_pass_static(const vamp_config* cfg, const dou
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     unsigned char* base = nullptr;
-    if (e == cudaSuccess) e = scratch_ptr(dev, &base);
+    if (e == cudaSuccess) e = scratch_ptr(&base);
     int maxsm = 0, sms = 0, bps = 0;
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e == cudaSuccess && ((int)smem > maxsm || cand.empty())) {

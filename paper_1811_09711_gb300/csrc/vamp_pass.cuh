@@ -444,6 +444,7 @@ PassVariant make_variant()
     v.D = D_;
     v.NB = NB_;
     v.minb = MINB;
+    v.family = "k_pass";
     v.fn[0] = (const void*)k_pass<T, 0, CPT, D_, NB_, MINB>;
     v.fn[1] = (const void*)k_pass<T, 1, CPT, D_, NB_, MINB>;
     v.launch = &pass_launch_t<T, CPT, D_, NB_, MINB>;

@@ -54,6 +54,7 @@ struct Req {
     int iterations = 0;
     int64_t calls = 0, n_events = 0, max_gen_calls = 0;
     unsigned char* records = nullptr;   // caller's buffer
+    double* state_out = nullptr;        // caller's buffer for the adapted state (optional)
     clk::time_point t_arrive, t_admit, t_done;
     // device state
     Params P{};
@@ -386,7 +387,27 @@ void tick_finish(vamp_server* s, const std::vector<Req*>& ints)
         r->calls_total += (int64_t)x[4];
         s->calls_done += (int64_t)x[4];
         if ((unsigned)x[8]) r->status = ((unsigned)x[8] & vamp::ERR_TIMEOUT) ? VAMP_ERR_TIMEOUT : VAMP_ERR_NUMERIC;
-        if (++r->it_done >= r->iterations) r->phase = r->n_events > 0 ? 2 : 3;
+        if (++r->it_done >= r->iterations) {
+            r->phase = r->n_events > 0 ? 2 : 3;
+            if (r->state_out && r->status == VAMP_OK) {
+                // the adapted state, copied on the request's stream before
+                // any generation batch (which leaves grids, α and shifts alone)
+                const Params& P = r->P;
+                const size_t ne = (size_t)P.K * P.d * (P.n + 1);
+                cudaError_t e = cudaMemcpyAsync(r->state_out, P.edges64, ne * 8, cudaMemcpyDeviceToDevice, r->stream);
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(r->state_out + ne, P.alpha, (size_t)P.K * 8, cudaMemcpyDeviceToDevice, r->stream);
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(r->state_out + ne + P.K, P.shift, (size_t)P.K * 8, cudaMemcpyDeviceToDevice,
+                                        r->stream);
+                if (e == cudaSuccess && r->phase == 3) {
+                    // no generation follows: completion waits for the copy
+                    e = cudaEventRecord(r->ev, r->stream);
+                    if (e == cudaSuccess) r->in_flight = true;
+                }
+                if (e != cudaSuccess) r->status = VAMP_ERR_CUDA;
+            }
+        }
     }
     ++s->n_ticks;
 }
@@ -608,12 +629,14 @@ vamp_status vamp_server_create(int32_t max_slots, int64_t mem_budget_bytes, int3
     return VAMP_OK;
 }
 
-vamp_status vamp_server_submit(vamp_server* s, const vamp_config* cfg, int32_t iterations, int64_t calls,
-                               int64_t n_events, int64_t max_gen_calls, void* dev_records, uint64_t* id_out)
+vamp_status vamp_server_submit_state(vamp_server* s, const vamp_config* cfg, int32_t iterations, int64_t calls,
+                                     int64_t n_events, int64_t max_gen_calls, void* dev_records, double* dev_state,
+                                     uint64_t* id_out)
 {
     if (!s || !cfg) return VAMP_ERR_INVALID_ARG;
     if (iterations < 1 || calls < 1 || n_events < 0 || max_gen_calls < 0) return VAMP_ERR_INVALID_ARG;
     if (n_events > 0 && (!dev_records || ((uintptr_t)dev_records & 7u))) return VAMP_ERR_INVALID_ARG;
+    if ((uintptr_t)dev_state & 7u) return VAMP_ERR_INVALID_ARG;
     Req* r = new (std::nothrow) Req();
     if (!r) return VAMP_ERR_OOM;
     r->cfg = *cfg;
@@ -631,7 +654,7 @@ vamp_status vamp_server_submit(vamp_server* s, const vamp_config* cfg, int32_t i
     }
     r->cfg.equiv = nullptr;  // copied into the setup; the caller's table may go away
     r->cfg.n_equiv = 0;
-    if (calls + (int64_t)r->P.K * r->P.n_min > int64_t(0xffffffff)) {
+    if (calls > int64_t(0xffffffff) || calls > int64_t(0xffffffff) - (int64_t)r->P.K * r->P.n_min) {
         delete r;
         return VAMP_ERR_INVALID_ARG;
     }
@@ -648,6 +671,7 @@ vamp_status vamp_server_submit(vamp_server* s, const vamp_config* cfg, int32_t i
     r->n_events = n_events;
     r->max_gen_calls = max_gen_calls;
     r->records = (unsigned char*)dev_records;
+    r->state_out = dev_state;
     r->t_arrive = clk::now();
     {
         std::lock_guard<std::mutex> lk(s->mu);
@@ -658,6 +682,13 @@ vamp_status vamp_server_submit(vamp_server* s, const vamp_config* cfg, int32_t i
     s->cv.notify_one();
     if (id_out) *id_out = r->id;
     return VAMP_OK;
+}
+
+vamp_status vamp_server_submit(vamp_server* s, const vamp_config* cfg, int32_t iterations, int64_t calls,
+                               int64_t n_events, int64_t max_gen_calls, void* dev_records, uint64_t* id_out)
+{
+    return vamp_server_submit_state(s, cfg, iterations, calls, n_events, max_gen_calls, dev_records, nullptr,
+                                    id_out);
 }
 
 int32_t vamp_server_poll(vamp_server* s, vamp_request_result* out, int32_t max_results)

@@ -128,7 +128,7 @@ bool build_setup(const vamp_config* cfg, Params& pr, Setup& S, std::string& why)
     if (!check_maps(cfg->channels, K, d, why) || !check_maps(cfg->peaks, P, d, why)) return false;
     if (!(cfg->gauss_sigma >= 0.0) || !std::isfinite(cfg->gauss_sigma)) { why = "gauss_sigma must be >= 0"; return false; }
     if (!(cfg->grid_alpha > 0.0) || !std::isfinite(cfg->beta)) { why = "grid_alpha must be > 0"; return false; }
-    if (cfg->n_min < 1) { why = "n_min must be >= 1"; return false; }
+    if (cfg->n_min < 1 || cfg->n_min > int64_t(0xffffffff)) { why = "n_min must be in 1..2^32-1"; return false; }
     if (cfg->gen_batch < 0 || cfg->gen_batch > (int64_t(1) << 24)) { why = "gen_batch out of range"; return false; }
     if (cfg->precision != VAMP_PREC_FP64 && cfg->precision != VAMP_PREC_FP32_EVAL) { why = "bad precision"; return false; }
     if (cfg->stratified != 0 && cfg->stratified != 1) { why = "stratified must be 0 or 1"; return false; }

@@ -91,15 +91,20 @@ class RequestResult(C.Structure):
 
 
 def load():
-    """Build (if stale) and load the CUDA library; raise if unusable."""
+    """Build (if the sources changed since the last build) and load the CUDA
+    library; raise if it is unusable or was not built from these sources."""
     global _lib
     with _lock:
         if _lib is not None:
             return _lib
-        path = _build.LIB
-        if not os.path.exists(path) or os.environ.get("VAMP_REBUILD"):
-            path = _build.build()
+        path = _build.build(force=bool(os.environ.get("VAMP_REBUILD")))
         lib = C.CDLL(path)
+        lib.vamp_source_hash.argtypes = []
+        lib.vamp_source_hash.restype = C.c_char_p
+        built_from, current = lib.vamp_source_hash().decode(), _build.source_hash()
+        if built_from != current:
+            raise RuntimeError(f"{path} was built from other sources (hash {built_from[:16]}, "
+                               f"sources {current[:16]}); rebuild with VAMP_REBUILD=1")
         vp, i32, i64, u32, dbl = C.c_void_p, C.c_int32, C.c_int64, C.c_uint32, C.c_double
         st = C.c_int
         lib.vamp_create.argtypes = [C.POINTER(Config), vp, C.POINTER(vp)]
@@ -136,6 +141,12 @@ def load():
         lib.vamp_pass_kernel_info.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32),
                                                 C.POINTER(i32), C.POINTER(i32)]
         lib.vamp_pass_kernel_info.restype = st
+        lib.vamp_pass_kernel_name.argtypes = [vp, i32, C.c_char_p, i32]
+        lib.vamp_pass_kernel_name.restype = st
+        lib.vamp_pass_kernel_candidates.argtypes = [vp, C.POINTER(i32)]
+        lib.vamp_pass_kernel_candidates.restype = st
+        lib.vamp_select_pass_kernel.argtypes = [vp, i32]
+        lib.vamp_select_pass_kernel.restype = st
         lib.vamp_batch_create.argtypes = [C.POINTER(Config), i32, i32, C.POINTER(vp)]
         lib.vamp_batch_create.restype = st
         lib.vamp_batch_iterate.argtypes = [vp, vp, u32, i32, C.POINTER(PassResult)]
@@ -152,6 +163,9 @@ def load():
         lib.vamp_server_create.restype = st
         lib.vamp_server_submit.argtypes = [vp, C.POINTER(Config), i32, i64, i64, i64, vp, C.POINTER(C.c_uint64)]
         lib.vamp_server_submit.restype = st
+        lib.vamp_server_submit_state.argtypes = [vp, C.POINTER(Config), i32, i64, i64, i64, vp, vp,
+                                                 C.POINTER(C.c_uint64)]
+        lib.vamp_server_submit_state.restype = st
         lib.vamp_server_poll.argtypes = [vp, C.POINTER(RequestResult), i32]
         lib.vamp_server_poll.restype = i32
         lib.vamp_server_wait_idle.argtypes = [vp, dbl]
@@ -216,6 +230,11 @@ def make_config(problem, precision: int = PREC_FP64):
                  int(problem.combine_from), int(precision), int(getattr(problem, "stratified", 0)),
                  int(eq.shape[0]), eq.ctypes.data_as(C.POINTER(C.c_int32)) if eq.shape[0] else None)
     return cfg, (ch, pk, w, eq)
+
+
+def source_hash() -> str:
+    """Hash of the sources the loaded library was built from (vamp_source_hash)."""
+    return load().vamp_source_hash().decode()
 
 
 def record_bytes(d: int) -> int:
@@ -320,11 +339,20 @@ class Vamp:
                 "ctas_per_sm": mb.value}
 
     def kernel_name(self, mode: int = 0) -> str:
-        """Name of the pass kernel as profilers print it."""
-        k = self.kernel_info()
-        t = "float" if k["fp32"] else "double"
-        return (f"k_pass<{t}, {mode}, {k['calls_per_thread']}, {k['shape_d']}, {k['shape_n']}, "
-                f"{k['ctas_per_sm']}>")
+        """Name of the pass kernel as profilers print it (vamp_pass_kernel_name)."""
+        buf = C.create_string_buffer(128)
+        self._check(self.lib.vamp_pass_kernel_name(self.h, int(mode), buf, 128))
+        return buf.value.decode()
+
+    def kernel_candidates(self) -> int:
+        """Number of compiled pass kernels that can run this problem (vamp_pass_kernel_candidates)."""
+        n = C.c_int32()
+        self._check(self.lib.vamp_pass_kernel_candidates(self.h, C.byref(n)))
+        return n.value
+
+    def select_kernel(self, index: int):
+        """Pin the pass kernel to candidate `index` (vamp_select_pass_kernel)."""
+        self._check(self.lib.vamp_select_pass_kernel(self.h, int(index)))
 
     # -- state ---------------------------------------------------------------
     def get_state(self, out=None):
@@ -458,11 +486,15 @@ class Server:
         self.h = h
 
     def submit(self, problem, iterations: int, calls: int, n_events: int = 0, records_ptr: int = 0,
-               max_gen_calls: int = 0) -> int:
+               max_gen_calls: int = 0, state_ptr: int = 0) -> int:
+        """Queue a request; ``state_ptr`` (device, K*d*(n+1) + 2K float64)
+        optionally receives the adapted grids, α and shifts
+        (vamp_server_submit_state)."""
         cfg, keep = make_config(problem, self.precision)
         rid = C.c_uint64()
-        rc = self.lib.vamp_server_submit(self.h, C.byref(cfg), int(iterations), int(calls), int(n_events),
-                                         int(max_gen_calls), C.c_void_p(records_ptr or None), C.byref(rid))
+        rc = self.lib.vamp_server_submit_state(self.h, C.byref(cfg), int(iterations), int(calls), int(n_events),
+                                               int(max_gen_calls), C.c_void_p(records_ptr or None),
+                                               C.c_void_p(state_ptr or None), C.byref(rid))
         del keep  # the server copied the description
         if rc != VAMP_OK:
             raise VampError(rc, "vamp_server_submit rejected the request")

@@ -38,6 +38,13 @@ def test_library_exports_every_declared_symbol(lib):
         assert hasattr(lib, n), n
 
 
+def test_library_is_bound_to_its_sources(lib):
+    """The loaded library carries the hash of the sources on disk, and the
+    build script records the same hash beside it."""
+    h = lib.vamp_source_hash().decode()
+    assert len(h) == 64 and h == B.source_hash() == B.recorded_hash()
+
+
 def test_status_strings_and_record_bytes(lib):
     assert lib.vamp_status_string(0) == b"VAMP_OK"
     assert lib.vamp_status_string(6) == b"VAMP_ERR_STATE"
@@ -56,7 +63,7 @@ def _create_status(lib, problem, **over):
 
 @pytest.mark.parametrize("field,value", [
     ("d", 0), ("d", 17), ("n_channels", 0), ("n_bins", 0), ("n_bins", 257), ("n_peaks", 0),
-    ("grid_alpha", 0.0), ("n_min", 0), ("gen_batch", -1), ("gen_batch", (1 << 24) + 1),
+    ("grid_alpha", 0.0), ("n_min", 0), ("n_min", 1 << 32), ("gen_batch", -1), ("gen_batch", (1 << 24) + 1),
     ("precision", 2), ("gauss_sigma", -1.0),
 ])
 def test_create_rejects_bad_config(lib, field, value):
