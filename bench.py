@@ -22,7 +22,13 @@ with autotuned and with fixed work items.  `serving`: a Poisson stream of
 integrate-then-generate requests (200 req/s over a 60 s arrival window,
 10 iterations each, 1e3..1e5 events each, 120 GB device budget) through the
 continuous-batching server, wall-clock throughput and p50/p99 latency, for
-the FP32-eval form and (over a shorter window) the FP64 form.
+the FP32-eval form, and for the FP64 form at an offered rate it sustains
+(16 req/s over 60 s).
+
+`roofline`: per pipe (32-bit lanes, shared-memory wavefronts, MUFU, FP64)
+the method's own work per call times the pass kernel's calls/s, against the
+pipe's throughput measured on the same GPU by small kernels
+(vamp_measure_peaks); `frac` is the binding pipe's fraction.
 
 `fp32_accuracy`: the FP32-eval pass against the FP64 pass on the same grids,
 α and random stream -- integral deviation (relative and in σ), and on a
@@ -51,14 +57,6 @@ sys.path.insert(0, ROOT)
 METRIC = "VAMP calls/s at d=14, 64 ch (FP32-eval vs FP64 path); p50/p99 request latency"
 UNIT = "calls/s"
 WORKLOAD = "collider_d14_k64_n100: d=14, K=64 channels (2-4 BW/power maps each), 64 peaks, 100 bins, 1e7 calls/iteration"
-
-
-def _peaks():
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            return json.load(f), "measured"
-    except Exception:
-        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
 class ClockSampler:
@@ -199,6 +197,42 @@ def algorithmic_ops_per_call(pr) -> float:
     K, d = pr.n_channels, pr.d
     mapped = int(sum(int(x) for x in pr.channels.n_mapped))
     return (8.0 * K * d + 15.0 * mapped + 7.0 * K + 8.0 * d + 60.0 * ((d + 3) // 4) + 10.0)
+
+
+def mapped_kinds(pr):
+    """Breit-Wigner and power-law mapped coordinates over all channels."""
+    ch = pr.channels
+    bw = pw = 0
+    for c in range(pr.n_channels):
+        for s in range(int(ch.n_mapped[c])):
+            k = int(ch.kind[c, s])
+            bw += k == 1
+            pw += k == 2
+    return bw, pw
+
+
+def xu_ops_per_call(pr) -> float:
+    """MUFU (special-function unit) operations of one call: one exp2 per
+    channel (its peak's Gaussian factor); per mapped coordinate one
+    reciprocal for a Breit-Wigner map (the Jacobian quotient), and two log2,
+    two exp2 and one reciprocal for a power map (x = p^0.2, the Jacobian,
+    the peak's (p + δ)^-0.8)."""
+    bw, pw = mapped_kinds(pr)
+    return float(pr.n_channels + bw + 5 * pw)
+
+
+def lsu_wavefronts_per_call(pr) -> float:
+    """Shared-memory load wavefronts of one call at the ideal one wavefront
+    per 32 lanes: the K*d bin lookups at three reads each (cell table, edge,
+    density)."""
+    return 3.0 * pr.n_channels * pr.d / 32.0
+
+
+def fp64_ops_per_call(pr) -> float:
+    """FP64 operations of one call in the FP32-eval form: the weight and its
+    square, the shifted sums (difference, sum, multiply-add), the maximum,
+    and one d-value addition per coordinate."""
+    return 6.0 + pr.d
 
 
 def cpu_oracle_rate(pr, seconds: float, threads: int):
@@ -526,28 +560,47 @@ def run_gpu(args):
         serving = {"fp32_eval": run_serving(V, P, torch, dev, V.PREC_FP32_EVAL, args.serve_rate, args.serve_seconds,
                                             120 * 10**9, args.serve_slots, 10, cap)}
         if args.serve_seconds_fp64 > 0:
-            serving["fp64"] = run_serving(V, P, torch, dev, V.PREC_FP64, args.serve_rate, args.serve_seconds_fp64,
-                                          120 * 10**9, args.serve_slots, 10, cap)
+            serving["fp64"] = run_serving(V, P, torch, dev, V.PREC_FP64, args.serve_rate_fp64,
+                                          args.serve_seconds_fp64, 120 * 10**9, args.serve_slots, 10, cap)
         serving["generation_call_limit"] = cap
 
     # ---- roofline of the dominant kernel (FP32-eval sampling kernel) ----------
-    peaks, src = _peaks()
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
-    peak_tops = n_sm * 128 * sm_max * 1e6 / 1e12  # lane-ops/s: 4 schedulers x 32 lanes per SM
+    # per pipe: the method's own work per call x calls per second of the
+    # kernel, against that pipe's throughput measured on this GPU
+    # (vamp_measure_peaks); the binding pipe's fraction is `frac`
+    mp = V.measure_peaks()
     k_ms = ks["sample_ms"] / max(ks["sample_launches"], 1)
-    ops = algorithmic_ops_per_call(pr) * (calls / max(args.steps, 1))
-    achieved = ops / (k_ms / 1e3) / 1e12
+    kcalls = calls / max(args.steps, 1) / (k_ms / 1e3)  # calls/s of the pass kernel
+    work = {"alu": (algorithmic_ops_per_call(pr), mp["fp32_lane_ops"], "Tops/s",
+                    "32-bit lane-operations (FP32 and integer) per call"),
+            "lsu": (lsu_wavefronts_per_call(pr), mp["lds_wavefronts"], "Twavefronts/s",
+                    "shared-memory load wavefronts per call (three 4-byte reads per lookup, 32 lanes each)"),
+            "xu": (xu_ops_per_call(pr), mp["xu_lane_ops"], "Tops/s", "MUFU operations per call"),
+            "fp64": (fp64_ops_per_call(pr), mp["fp64_lane_ops"], "Tops/s", "FP64 operations per call")}
+    pipes = {}
+    for name, (per_call, peak, unit, what) in work.items():
+        ach = per_call * kcalls
+        pipes[name] = {"achieved": ach / 1e12, "peak": peak / 1e12, "unit": unit, "frac": ach / peak,
+                       "per_call": per_call, "work": what}
+    bound = max(pipes, key=lambda k: pipes[k]["frac"])
     kname = g.kernel_name()
-    roof = {"bound": "alu", "achieved": achieved, "peak": peak_tops, "unit": "Tops/s",
-            "frac": achieved / peak_tops, "traffic": measured_traffic(kname),
-            "kernel": kname, "kernel_ms": k_ms,
-            "ops_per_call": algorithmic_ops_per_call(pr),
-            "frac_lookups_only": lookup_ops_per_call(pr) * (calls / max(args.steps, 1)) / (k_ms / 1e3) / 1e12 / peak_tops,
-            "peak_source": f"{n_sm} SMs x 128 lanes x {sm_max:.0f} MHz ({src} max clock)"}
+    bp = pipes[bound]
+    roof = {"bound": bound, "achieved": bp["achieved"], "peak": bp["peak"], "unit": bp["unit"],
+            "frac": bp["frac"], "traffic": measured_traffic(kname),
+            "kernel": kname, "kernel_ms": k_ms, "ops_per_call": algorithmic_ops_per_call(pr),
+            "frac_lookups_only": lookup_ops_per_call(pr) * kcalls / mp["fp32_lane_ops"],
+            "pipes": pipes,
+            "peak_source": "measured on this GPU by vamp_measure_peaks (FFMA, DFMA, MUFU and conflict-free "
+                           "shared-load kernels)"}
     if batch is not None:
         for tag in ("tuned", "fixed"):
-            batch[tag]["frac_of_alu_peak"] = batch[tag]["alu_ops_per_s"] / (peak_tops * 1e12)
+            batch[tag]["frac_of_alu_peak"] = batch[tag]["alu_ops_per_s"] / mp["fp32_lane_ops"]
+    # the FP64 form: the same algorithmic operations, all in FP64, against the
+    # measured FP64 FMA lane rate
+    fp64_ops = algorithmic_ops_per_call(pr) * fp64_rate
+    fp64_roof = {"bound": "fp64", "achieved": fp64_ops / 1e12, "peak": mp["fp64_lane_ops"] / 1e12,
+                 "unit": "Tops/s", "frac": fp64_ops / mp["fp64_lane_ops"],
+                 "peak_source": "measured on this GPU by vamp_measure_peaks (DFMA kernel)"}
 
     res = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
@@ -558,7 +611,9 @@ def run_gpu(args):
                                 "the replay); kernel times for the roofline from an event-timed run of the same "
                                 "iterations from the same state",
                       "precision": "FP32-eval"},
-           "fp64_path": {"value": fp64_rate, "unit": UNIT, "speedup_fp32_eval": value / ws / fp64_rate},
+           "fp64_path": {"value": fp64_rate, "unit": UNIT, "speedup_fp32_eval": value / ws / fp64_rate,
+                         "roofline": fp64_roof},
+           "measured_peaks": mp,
            "fp32_accuracy": fp32_acc,
            "generation": {"events": gst["n_written"], "events_per_s": gst["n_written"] / (gen_ms / 1e3),
                           "calls_used": gst["n_calls_used"], "overweight": gst["n_overweight"],
@@ -596,8 +651,10 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--batch-iters", type=int, default=3, help="timed iterations of the 256-instance batch (0: skip)")
     ap.add_argument("--serve-seconds", type=float, default=60.0, help="arrival window of the request stream (0: skip)")
-    ap.add_argument("--serve-seconds-fp64", type=float, default=1.0, help="arrival window for the FP64 form")
+    ap.add_argument("--serve-seconds-fp64", type=float, default=60.0, help="arrival window for the FP64 form")
     ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--serve-rate-fp64", type=float, default=16.0,
+                    help="offered rate of the FP64 form (below the rate it sustains)")
     ap.add_argument("--serve-slots", type=int, default=256)
     args = ap.parse_args()
     if args.impl == "reference":

@@ -288,6 +288,23 @@ vamp_status vamp_kernel_stats(vamp_ctx *ctx, double *sample_ms, int64_t *sample_
 vamp_status vamp_pass_kernel_info(const vamp_ctx *ctx, int32_t *fp32, int32_t *calls_per_thread,
                                   int32_t *shape_d, int32_t *shape_n, int32_t *ctas_per_sm);
 
+/* Throughput of this GPU's pipes, measured by small kernels that keep one
+ * pipe busy (for the per-pipe roofline of the sampling kernel; the paper has
+ * no counterpart).  Per second, summed over all SMs: FP32 fused
+ * multiply-add lane-instructions (the issue rate of 32-bit arithmetic),
+ * FP64 fused multiply-add lane-instructions, MUFU (special-function unit)
+ * lane-instructions (2^x), and shared-memory load wavefronts (one per warp
+ * load of 32 consecutive words).  Runs on the current device and
+ * synchronises it; takes a few tens of milliseconds.  OOM / CUDA on
+ * failure. */
+typedef struct vamp_pipe_peaks {
+    double fp32_lane_ops;
+    double fp64_lane_ops;
+    double xu_lane_ops;
+    double lds_wavefronts;
+} vamp_pipe_peaks;
+vamp_status vamp_measure_peaks(vamp_pipe_peaks *out);
+
 /* Name of the pass kernel the context uses for mode 0 (integration) or 1
  * (generation), as profilers print it, e.g. "k_pass<float, 0, 2, 14, 100, 2>",
  * written NUL-terminated into buf (len bytes, host).  INVALID_ARG for a bad
@@ -434,7 +451,9 @@ void vamp_server_destroy(vamp_server *s);
  * unpredictably).  The paper has no counterpart: it is an interface addition
  * of this library.  (Host-side set-up uses small temporary heap buffers.)
  *
- * Same pass as vamp_sample_pass, without a context: the caller passes the
+ * Same pass as vamp_sample_pass, without a context, run by the first
+ * candidate kernel of the shape (vamp_pass_kernel_candidates order; a
+ * context pinned to it gives the same sums): the caller passes the
  * problem (cfg, host memory, read during the call), the grid state in device
  * memory -- dev_edges [K][d][n+1], dev_alpha [K], dev_shift [K] (previous
  * pass means, zeros for a first pass), all read only -- and the outputs:

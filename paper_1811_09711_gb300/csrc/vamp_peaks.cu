@@ -1,0 +1,150 @@
+// vamp_peaks.cu -- vamp_measure_peaks: the per-pipe throughput of this GPU
+// measured with small kernels, the denominators of the benchmark's
+// per-pipe roofline (FP32 lanes, FP64 lanes, the MUFU special-function unit
+// and shared-memory load wavefronts).
+//
+// Each kernel runs enough independent dependency chains per thread to keep
+// its pipe busy, over a grid of every SM's resident CTAs, and is timed with
+// CUDA events; the count of executed operations over the time is the peak.
+#include "../../include/vamp.h"
+
+#include <cuda_runtime.h>
+
+namespace {
+
+constexpr int PK_THREADS = 256;
+constexpr int PK_CHAINS = 8;
+
+__global__ void __launch_bounds__(PK_THREADS) k_peak_ffma(float* out, float b, float c, int iters)
+{
+    float a[PK_CHAINS];
+#pragma unroll
+    for (int i = 0; i < PK_CHAINS; ++i) a[i] = (float)(threadIdx.x + i) * 1e-3f;
+    for (int r = 0; r < iters; ++r)
+#pragma unroll
+        for (int i = 0; i < PK_CHAINS; ++i) a[i] = fmaf(a[i], b, c);
+    float s = 0.f;
+#pragma unroll
+    for (int i = 0; i < PK_CHAINS; ++i) s += a[i];
+    out[blockIdx.x * PK_THREADS + threadIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(PK_THREADS) k_peak_dfma(double* out, double b, double c, int iters)
+{
+    double a[PK_CHAINS];
+#pragma unroll
+    for (int i = 0; i < PK_CHAINS; ++i) a[i] = (double)(threadIdx.x + i) * 1e-3;
+    for (int r = 0; r < iters; ++r)
+#pragma unroll
+        for (int i = 0; i < PK_CHAINS; ++i) a[i] = fma(a[i], b, c);
+    double s = 0.0;
+#pragma unroll
+    for (int i = 0; i < PK_CHAINS; ++i) s += a[i];
+    out[blockIdx.x * PK_THREADS + threadIdx.x] = s;
+}
+
+__device__ __forceinline__ float ex2_approx(float v)
+{
+    float r;
+    asm volatile("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+    return r;
+}
+
+// MUFU: x <- 2^x * c keeps x in (0, 1] for c = 0.5 (one FMUL per MUFU op,
+// on the FMA pipe, which has eight times the MUFU rate)
+__global__ void __launch_bounds__(PK_THREADS) k_peak_mufu(float* out, float c, int iters)
+{
+    float a[PK_CHAINS];
+#pragma unroll
+    for (int i = 0; i < PK_CHAINS; ++i) a[i] = (float)(threadIdx.x % 7 + i) * 0.1f;
+    for (int r = 0; r < iters; ++r)
+#pragma unroll
+        for (int i = 0; i < PK_CHAINS; ++i) a[i] = ex2_approx(a[i]) * c;
+    float s = 0.f;
+#pragma unroll
+    for (int i = 0; i < PK_CHAINS; ++i) s += a[i];
+    out[blockIdx.x * PK_THREADS + threadIdx.x] = s;
+}
+
+// Shared-memory loads: each warp reads 32 consecutive words (one wavefront
+// per load instruction, no bank conflict)
+constexpr int PK_SMEM_WORDS = 4096;
+__global__ void __launch_bounds__(PK_THREADS) k_peak_lds(unsigned* out, int iters)
+{
+    __shared__ unsigned s[PK_SMEM_WORDS];
+    for (int i = threadIdx.x; i < PK_SMEM_WORDS; i += PK_THREADS) s[i] = (unsigned)i * 2654435761u;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    unsigned acc[PK_CHAINS];
+#pragma unroll
+    for (int i = 0; i < PK_CHAINS; ++i) acc[i] = 0u;
+    // chain i of step r reads row ((w + r) 8 + i) mod ROWS: rows come in
+    // groups of eight, so one base register plus an immediate addresses
+    // them (two instructions per load: the loads, not the issue rate, bind)
+    constexpr int ROWS = PK_SMEM_WORDS / 32;
+    for (int r = 0; r < iters; ++r) {
+        const unsigned* rb = s + ((((w + r) * PK_CHAINS) & (ROWS - 1)) * 32 + lane);
+#pragma unroll
+        for (int i = 0; i < PK_CHAINS; ++i) acc[i] += rb[i * 32];
+    }
+    unsigned t = 0u;
+#pragma unroll
+    for (int i = 0; i < PK_CHAINS; ++i) t ^= acc[i];
+    out[blockIdx.x * PK_THREADS + threadIdx.x] = t;
+}
+
+template <typename F>
+cudaError_t time_kernel(F launch, float* ms)
+{
+    cudaEvent_t e0, e1;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) return e;
+    launch();  // warm-up
+    e = cudaEventRecord(e0);
+    if (e == cudaSuccess) launch();
+    if (e == cudaSuccess) e = cudaEventRecord(e1);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaEventElapsedTime(ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return e;
+}
+
+}  // namespace
+
+extern "C" vamp_status vamp_measure_peaks(vamp_pipe_peaks* out)
+{
+    if (!out) return VAMP_ERR_INVALID_ARG;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return VAMP_ERR_CUDA;
+    int bf = 0, bd = 0, bm = 0, bl = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bf, k_peak_ffma, PK_THREADS, 0) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bd, k_peak_dfma, PK_THREADS, 0) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bm, k_peak_mufu, PK_THREADS, 0) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bl, k_peak_lds, PK_THREADS, 0) != cudaSuccess)
+        return VAMP_ERR_CUDA;
+    const int grid = sms * (bf > 0 ? bf : 1);
+    const int gd = sms * (bd > 0 ? bd : 1), gm = sms * (bm > 0 ? bm : 1), gl = sms * (bl > 0 ? bl : 1);
+    const int maxg = grid > gd ? (grid > gm ? (grid > gl ? grid : gl) : (gm > gl ? gm : gl)) : (gd > gm ? (gd > gl ? gd : gl) : (gm > gl ? gm : gl));
+    void* buf = nullptr;
+    if (cudaMalloc(&buf, (size_t)maxg * PK_THREADS * 8) != cudaSuccess) return VAMP_ERR_OOM;
+    vamp_status st = VAMP_OK;
+    float ms = 0.f;
+    const int it_f = 1 << 16, it_d = 1 << 12, it_m = 1 << 13, it_l = 1 << 14;
+    cudaError_t e = time_kernel([&] { k_peak_ffma<<<grid, PK_THREADS>>>((float*)buf, 0.9999f, 1e-4f, it_f); }, &ms);
+    if (e == cudaSuccess) out->fp32_lane_ops = (double)grid * PK_THREADS * PK_CHAINS * it_f / (ms * 1e-3);
+    if (e == cudaSuccess)
+        e = time_kernel([&] { k_peak_dfma<<<gd, PK_THREADS>>>((double*)buf, 0.9999, 1e-4, it_d); }, &ms);
+    if (e == cudaSuccess) out->fp64_lane_ops = (double)gd * PK_THREADS * PK_CHAINS * it_d / (ms * 1e-3);
+    if (e == cudaSuccess) e = time_kernel([&] { k_peak_mufu<<<gm, PK_THREADS>>>((float*)buf, 0.5f, it_m); }, &ms);
+    if (e == cudaSuccess) out->xu_lane_ops = (double)gm * PK_THREADS * PK_CHAINS * it_m / (ms * 1e-3);
+    if (e == cudaSuccess) e = time_kernel([&] { k_peak_lds<<<gl, PK_THREADS>>>((unsigned*)buf, it_l); }, &ms);
+    if (e == cudaSuccess) out->lds_wavefronts = (double)gl * (PK_THREADS / 32) * PK_CHAINS * it_l / (ms * 1e-3);
+    if (e != cudaSuccess) st = VAMP_ERR_CUDA;
+    cudaFree(buf);
+    return st;
+}

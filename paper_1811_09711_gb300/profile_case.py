@@ -7,7 +7,7 @@
 adaptation iterations of `calls` calls (pass, rebinning, α update), then
 `events` unweighted events if asked.  The first pass also times the pass
 kernel variants (the autotuner's probe launches come before it: two per
-candidate kernel).  ``batch``: the first `instances` instances of the
+candidate kernel) unless `--kernel` pins one.  ``batch``: the first `instances` instances of the
 256-instance uneven batch, `iterations` iterations with the work-item shape
 fixed (no autotuner launches).  Prints one line and exits 0 on success.
 """
@@ -29,10 +29,19 @@ def main() -> int:
     ap.add_argument("--precision", type=int, default=V.PREC_FP32_EVAL)
     ap.add_argument("--events", type=int, default=0)
     ap.add_argument("--instances", type=int, default=64)
+    ap.add_argument("--kernel", default="",
+                    help="pin the pass kernel: a kernel name or its start, e.g. k_scan or 'k_pass<float, 0, 2'")
     a = ap.parse_args()
     if a.workload == "collider":
         pr = P.collider()
         g = V.Vamp(pr, precision=a.precision)
+        if a.kernel:
+            for i in range(g.kernel_candidates()):
+                g.select_kernel(i)
+                if g.kernel_name().startswith(a.kernel):
+                    break
+            else:
+                raise SystemExit(f"no candidate kernel named {a.kernel!r}")
         for it in range(a.iterations):
             r = g.sample_pass(int(a.calls), it)
             g.refine_grids()

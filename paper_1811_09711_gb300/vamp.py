@@ -83,6 +83,11 @@ class PassResult(C.Structure):
         return f"PassResult({self.as_dict()})"
 
 
+class PipePeaks(C.Structure):
+    _fields_ = [("fp32_lane_ops", C.c_double), ("fp64_lane_ops", C.c_double), ("xu_lane_ops", C.c_double),
+                ("lds_wavefronts", C.c_double)]
+
+
 class RequestResult(C.Structure):
     _fields_ = [("id", C.c_uint64), ("status", C.c_int32), ("iterations", C.c_int32),
                 ("result", PassResult), ("calls_total", C.c_int64), ("events_written", C.c_int64),
@@ -141,6 +146,8 @@ def load():
         lib.vamp_pass_kernel_info.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32),
                                                 C.POINTER(i32), C.POINTER(i32)]
         lib.vamp_pass_kernel_info.restype = st
+        lib.vamp_measure_peaks.argtypes = [C.POINTER(PipePeaks)]
+        lib.vamp_measure_peaks.restype = st
         lib.vamp_pass_kernel_name.argtypes = [vp, i32, C.c_char_p, i32]
         lib.vamp_pass_kernel_name.restype = st
         lib.vamp_pass_kernel_candidates.argtypes = [vp, C.POINTER(i32)]
@@ -354,6 +361,18 @@ class Vamp:
         """Pin the pass kernel to candidate `index` (vamp_select_pass_kernel)."""
         self._check(self.lib.vamp_select_pass_kernel(self.h, int(index)))
 
+    def select_family(self, family: str) -> str:
+        """Pin the pass kernel to the first candidate of a kernel family
+        ("k_pass": the channel loop per call, whose FP32-eval arithmetic the
+        batch and server kernels share; "k_scan": lookups per coordinate);
+        returns its name."""
+        for i in range(self.kernel_candidates()):
+            self.select_kernel(i)
+            name = self.kernel_name(0)
+            if name.startswith(family + "<"):
+                return name
+        raise VampError(VAMP_ERR_INVALID_ARG, f"no {family} kernel for this problem")
+
     # -- state ---------------------------------------------------------------
     def get_state(self, out=None):
         """Grids, α, shifts and w_max (vamp_get_state).  ``out``: optional dict
@@ -530,6 +549,17 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def measure_peaks() -> dict:
+    """vamp_measure_peaks: measured per-pipe throughput of the current GPU
+    (per second, all SMs): FP32 and FP64 FMA lane-instructions, MUFU
+    lane-instructions, shared-memory load wavefronts."""
+    pk = PipePeaks()
+    rc = load().vamp_measure_peaks(C.byref(pk))
+    if rc != VAMP_OK:
+        raise VampError(rc, "vamp_measure_peaks failed")
+    return {k: getattr(pk, k) for k, _ in PipePeaks._fields_}
 
 
 def selftest_bounded_wait(limit_cycles: int):

@@ -36,6 +36,8 @@ def test_batch_equals_alone(precision, tol):
     probs = _instances(14)
     batch = V.Batch(probs, precision=precision, autotune=True)
     alone = [V.Vamp(pr, precision=precision) for pr in probs]
+    for g in alone:
+        g.select_family("k_pass")  # the FP32-eval arithmetic of the batch kernel
     worst = 0.0
     for it in range(3):
         ncalls = [pr.calls for pr in probs]

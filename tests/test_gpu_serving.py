@@ -28,6 +28,7 @@ def _requests(n, seed=11, min_calls=20000, div=20):
 def _alone(V, pr, iters, calls, n_ev, precision):
     import torch
     g = V.Vamp(pr, precision=precision)
+    g.select_family("k_pass")  # the FP32-eval arithmetic of the server's multi-instance kernel
     r = None
     for it in range(iters):
         r = g.sample_pass(calls, it)

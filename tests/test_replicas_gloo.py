@@ -74,3 +74,20 @@ def test_roofline_operation_counts():
     assert (K, d, mapped) == (64, 14, 188)
     assert bench.lookup_ops_per_call(pr) == 8 * K * d == 7168
     assert bench.algorithmic_ops_per_call(pr) == 8 * K * d + 15 * mapped + 7 * K + 8 * d + 60 * 4 + 10 == 10798
+
+
+def test_roofline_per_pipe_work():
+    """Per-pipe work per call charged to the roofline: MUFU operations (one
+    exp2 per channel, one reciprocal per Breit-Wigner map, five per power
+    map), shared-memory wavefronts (three 4-byte reads per lookup at 32
+    lanes per wavefront) and FP64 operations of the FP32-eval form."""
+    import bench
+    from paper_1811_09711_gb300 import problems as P
+    pr = P.collider()
+    ch = pr.channels
+    kinds = [int(ch.kind[c, s]) for c in range(pr.n_channels) for s in range(int(ch.n_mapped[c]))]
+    bw, pw = kinds.count(P.MAP_BW), kinds.count(P.MAP_POW)
+    assert bw + pw == 188 and bench.mapped_kinds(pr) == (bw, pw)
+    assert bench.xu_ops_per_call(pr) == 64 + bw + 5 * pw
+    assert bench.lsu_wavefronts_per_call(pr) == 3 * 64 * 14 / 32 == 84.0
+    assert bench.fp64_ops_per_call(pr) == 20.0
