@@ -214,8 +214,42 @@ template <> struct Prec<double> {
     }
     static __device__ __forceinline__ double tan_(double v) { return tan(v); }
     static __device__ __forceinline__ double atan_(double v) { return atan(v); }
-    static __device__ __forceinline__ double pow02(double v) { return pow(v, 0.2); }
-    static __device__ __forceinline__ double powm08(double v) { return pow(v, -0.8); }
+    // v^(-1/5) for a normal v > 0 (Newton's method for the inverse fifth
+    // root): with v = m 2^E, m in [1, 2), write -E = 5a + r (r in 0..4), so
+    // v^(-1/5) = 2^a w^(-1/5) with w = m 2^-r in [1/16, 2).  The seed
+    // 2^(-0.2 log2 w) comes from the FP32 special-function approximations
+    // (relative error about 1e-7); two division-free Newton steps for
+    // y^-5 = w, y <- y (6 - w y^5) / 5, each squaring the relative error,
+    // bring it to a few units in the last place.
+    static __device__ __forceinline__ double rinv5(double v)
+    {
+        const long long b = __double_as_longlong(v);
+        const int ne = 1023 - (int)((b >> 52) & 0x7ff);  // -E
+        const int a = ne >= 0 ? ne / 5 : -((4 - ne) / 5);
+        const int r = ne - 5 * a;
+        const double w = __longlong_as_double((b & 0x000FFFFFFFFFFFFFll) | ((long long)(1023 - r) << 52));
+        float s;
+        asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(s) : "f"(-0.2f * __log2f((float)w)));
+        double y = (double)s;
+#pragma unroll
+        for (int it = 0; it < 2; ++it) {
+            const double y2 = y * y, y4 = y2 * y2;
+            y = y * fma(-w, y4 * y, 6.0) * 0.2;
+        }
+        return y * __longlong_as_double((long long)(1023 + a) << 52);  // times 2^a
+    }
+    // v^0.2 = v (v^(-1/5))^4
+    static __device__ __forceinline__ double pow02(double v)
+    {
+        const double y = rinv5(v), y2 = y * y;
+        return v * (y2 * y2);
+    }
+    // v^-0.8 = (v^(-1/5))^4
+    static __device__ __forceinline__ double powm08(double v)
+    {
+        const double y = rinv5(v), y2 = y * y;
+        return y2 * y2;
+    }
     static __device__ __forceinline__ double exp2_(double v) { return exp2(v); }
     static __device__ __forceinline__ double div(double a, double b) { return a / b; }
     static __device__ __forceinline__ double tiny() { return 2.2250738585072014e-308; }
@@ -488,10 +522,18 @@ __device__ __forceinline__ void channel_rows(const Params& P, const SH& sh, cons
                     const T del = sp[SP_DEL], ipn = sp[SP_INVPOWN];
 #pragma unroll
                     for (int q = 0; q < CPT; ++q) {
-                        const T xx = Prec<T>::pow02(p[q][k]);
-                        const T x2 = xx * xx;
-                        J[q] *= Prec<T>::div(T(1), T(5) * (x2 * x2));
-                        xk[q] = xx;
+                        if constexpr (sizeof(T) == 8) {
+                            // x = p^0.2 = p y^4 and 1/φ' = 1/(5 x^4) = y^4 / 5 from
+                            // y = p^(-1/5): no division, no pow
+                            const T y = Prec<T>::rinv5(p[q][k]), y2 = y * y, y4 = y2 * y2;
+                            J[q] *= T(0.2) * y4;
+                            xk[q] = p[q][k] * y4;
+                        } else {
+                            const T xx = Prec<T>::pow02(p[q][k]);
+                            const T x2 = xx * xx;
+                            J[q] *= Prec<T>::div(T(1), T(5) * (x2 * x2));
+                            xk[q] = xx;
+                        }
                         if (with_f) F[q] *= Prec<T>::powm08(p[q][k] + del) * ipn;
                         const T u = p[q][k] - gc;
                         as[q] += u * u * k2;

@@ -339,3 +339,42 @@ def test_contexts_with_different_shapes_coexist(V, O):
     rb = big.sample_pass(20_000, 0)
     rs = small.sample_pass(10_000, 0)
     assert rb.n_calls > 0 and rs.n_calls == 10_000
+
+
+# --------------------------------------------------------------------------
+# FP64 power-law maps: the inverse fifth root by Newton's method against the
+# oracle's pow() (libm), over the exponent range the range reduction spans
+# --------------------------------------------------------------------------
+def test_fp64_power_maps_match_libm_pow(V, O):
+    """Channels mapping by x^5 with δ = 0, 1e-3 and 5 (so p + δ spans
+    [2^-1022, 6]); per-call bins bit-exact, coordinates, g, f and weights
+    within 1e-13 of the oracle, whose maps call pow()."""
+    ms = P.MapSet.identity(3)
+    for c, dl in enumerate((0.0, 1e-3, 5.0)):
+        ms.n_mapped[c] = 1
+        ms.coord[c, 0] = c
+        ms.kind[c, 0] = P.MAP_POW
+        ms.b[c, 0] = dl
+    pr = P.Problem(name="pow3", d=3, n_bins=30, channels=ms, peak_weight=np.array([0.5, 0.3, 0.2]),
+                   peaks=ms.copy(), gauss_sigma=0.2, gauss_centre=0.5, gauss_norm=P.GAUSS_NORM_UNIT, seed=4,
+                   iterations=3, calls=20_000, adapt_grid=True, adapt_alpha=True)
+    o = O.Oracle(pr)
+    for it in range(2):
+        o.sample_pass(20_000, it, n_threads=NTHREADS)
+        o.refine_grids()
+        o.update_alpha()
+    st = o.get_state()
+    g = V.Vamp(pr)
+    g.set_state(st["edges"], st["alpha"], st["shift"], st["w_max"])
+    assert g.allocate(100_000) == o.allocate(100_000)
+    r = g.eval_calls(0, 3, 0, 3000)
+    worst = 0.0
+    for q in range(3000):
+        ref = o.eval_call(0, 3, q)
+        assert np.array_equal(r["bins"][q], ref["bins"]), q
+        for key in ("x", "p"):
+            assert rel(r[key][q], ref[key]) < 1e-13, (key, q)
+        for key in ("f", "g", "w"):
+            worst = max(worst, rel(r[key][q], ref[key]))
+    print(f"\nFP64 power-law maps: largest relative deviation of f, g, w from the oracle {worst:.2e}")
+    assert worst < 1e-13

@@ -91,3 +91,15 @@ def test_roofline_per_pipe_work():
     assert bench.xu_ops_per_call(pr) == 64 + bw + 5 * pw
     assert bench.lsu_wavefronts_per_call(pr) == 3 * 64 * 14 / 32 == 84.0
     assert bench.fp64_ops_per_call(pr) == 20.0
+
+
+def test_fp64_form_operation_count():
+    """Floating-point work per call of the FP64 form, term by term: one
+    density product per lookup, 12 per Breit-Wigner map, 14 per power map,
+    7 per channel, 4 per coordinate, 10 for the weight and sums."""
+    import bench
+    from paper_1811_09711_gb300 import problems as P
+    pr = P.collider()
+    bw, pw = bench.mapped_kinds(pr)
+    assert bench.fp64_form_ops_per_call(pr) == 64 * 14 + 12 * bw + 14 * pw + 7 * 64 + 4 * 14 + 10
+    assert bench.fp64_form_ops_per_call(pr) == 3850
