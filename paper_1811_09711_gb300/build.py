@@ -24,8 +24,9 @@ LIB = os.path.join(LIBDIR, "libvamp_gb300.so")
 HASH_FILE = os.path.join(LIBDIR, "libvamp_gb300.sha256")
 SOURCES = ["vamp_api.cu", "vamp_setup.cu", "vamp_kernels.cu", "vamp_noalloc.cu", "vamp_pass_f32.cu",
            "vamp_pass_f32_shapes.cu", "vamp_pass_f64.cu", "vamp_batch.cu", "vamp_batch_pass.cu",
-           "vamp_server.cu", "vamp_peaks.cu"]
-HEADERS = ["vamp_device.cuh", "vamp_internal.h", "vamp_pass.cuh", os.path.join("..", "..", "include", "vamp.h")]
+           "vamp_server.cu", "vamp_peaks.cu", "vamp_union.cu"]
+HEADERS = ["vamp_device.cuh", "vamp_internal.h", "vamp_pass.cuh", "vamp_union.cuh",
+           os.path.join("..", "..", "include", "vamp.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

@@ -34,6 +34,8 @@ struct vamp_ctx {
     size_t smem_pass = 0;      // dynamic shared memory of the integration pass kernel
     size_t smem_gen = 0;       // ... of the generation pass kernel
     const PassVariant* var = nullptr;  // pass kernels in use
+    void* uni_buf = nullptr;   // interval tables of the union pass (allocated while such a kernel is in use)
+    int uni_on = 0;            // the tables exist and follow every grid change
     int tuned = 0;             // var was chosen by timing (first sampling pass)
     int64_t cell_cap = 0;      // cells the stratified-pass cell sums hold
     int grid_pass = 0;         // persistent grid of the integration pass kernel
@@ -143,13 +145,57 @@ struct VariantShape {
 VariantShape shape_of(const vamp_ctx* c, const PassVariant* v)
 {
     VariantShape s{};
+    if (v->uni) {
+        s.tile = 1;
+        s.smem_pass = vamp::union_pass_smem(c->prm, *v, 0);
+        s.smem_gen = vamp::union_pass_smem(c->prm, *v, 1);
+        return s;
+    }
     vamp::pass_smem_for(c->prm, c->fp32, v->minb, &s.tile, &s.smem_pass, &s.smem_gen);
     return s;
+}
+
+// Allocates the union pass's interval tables (once) and enqueues their
+// build from the current grids; from then on every grid change rebuilds them.
+vamp_status union_enable(vamp_ctx* c)
+{
+    if (!c->uni_buf) {
+        void* b = nullptr;
+        if (cudaMalloc(&b, vamp::union_bytes(c->d, c->K, c->n)) != cudaSuccess)
+            return fail(c, VAMP_ERR_OOM, "interval tables of the union pass");
+        c->uni_buf = b;
+        vamp::bind_union(c->prm, (unsigned char*)b);
+    }
+    VAMP_CK(c, vamp::launch_union_build(c->prm, c->stream));
+    c->uni_on = 1;
+    return VAMP_OK;
+}
+
+void union_disable(vamp_ctx* c)
+{
+    if (c->uni_buf) {
+        cudaStreamSynchronize(c->stream);
+        cudaFree(c->uni_buf);
+    }
+    c->uni_buf = nullptr;
+    c->uni_on = 0;
+    vamp::bind_union(c->prm, nullptr);
+}
+
+std::vector<const PassVariant*> candidates_of(const vamp_ctx* c)
+{
+    return vamp::pass_candidates(c->fp32, c->d, c->n, c->prm.stratified, c->K);
 }
 
 // Makes v the context's pass kernel: its tile, shared memory and grids.
 vamp_status use_variant(vamp_ctx* c, const PassVariant* v)
 {
+    if (v->uni && !c->uni_on) {
+        const vamp_status us = union_enable(c);
+        if (us != VAMP_OK) return us;
+    } else if (!v->uni && c->uni_on) {
+        union_disable(c);
+    }
     const VariantShape s = shape_of(c, v);
     VAMP_CK(c, vamp::ensure_smem(v->fn[0], s.smem_pass));
     VAMP_CK(c, vamp::ensure_smem(v->fn[1], s.smem_gen));
@@ -167,7 +213,7 @@ vamp_status use_variant(vamp_ctx* c, const PassVariant* v)
 
 vamp_status choose_variant(vamp_ctx* c, int64_t n_calls)
 {
-    const std::vector<const PassVariant*> cand = vamp::pass_candidates(c->fp32, c->d, c->n, c->prm.stratified);
+    const std::vector<const PassVariant*> cand = candidates_of(c);
     if (cand.empty()) return fail(c, VAMP_ERR_INVALID_ARG, "no pass kernel for this shape");
     for (const PassVariant* v : cand) {
         const VariantShape s = shape_of(c, v);
@@ -198,6 +244,11 @@ vamp_status choose_variant(vamp_ctx* c, int64_t n_calls)
         // time each candidate on a pass of `probe` calls over the current
         // grids; the pass result is discarded (no finish kernel runs) and
         // the accumulators are cleared again below
+        for (const PassVariant* v : cand)
+            if (v->uni && !c->uni_on) {
+                const vamp_status us = union_enable(c);
+                if (us != VAMP_OK) return us;
+            }
         cudaEvent_t e0, e1;
         VAMP_CK(c, cudaEventCreate(&e0));
         VAMP_CK(c, cudaEventCreate(&e1));
@@ -269,6 +320,7 @@ void vamp_destroy(vamp_ctx* c)
         DeviceGuard g(c->dev);
         if (c->stream) cudaStreamSynchronize(c->stream);
         cudaFree(c->arena);
+        cudaFree(c->uni_buf);
         cudaFree(c->prm.cellsum);
         cudaFree(c->g_staging);
         cudaFree(c->g_callidx);
@@ -336,7 +388,7 @@ vamp_status vamp_create(const vamp_config* cfg, void* cuda_stream, vamp_ctx** ou
         CREATE_CK(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->dev));
         // until the first pass picks by timing: the first candidate (the
         // shape-specialised kernel if there is one)
-        const std::vector<const PassVariant*> cand = vamp::pass_candidates(c->fp32, c->d, c->n, c->prm.stratified);
+        const std::vector<const PassVariant*> cand = candidates_of(c);
         if (cand.empty()) { st = fail(c, VAMP_ERR_INVALID_ARG, "no pass kernel for this shape"); goto create_fail; }
         st = use_variant(c, cand[0]);
         if (st != VAMP_OK) goto create_fail;
@@ -463,6 +515,7 @@ vamp_status vamp_refine_grids(vamp_ctx* c)
     if (!c->have_pass) return fail(c, VAMP_ERR_STATE, "refine before any sampling pass");
     DeviceGuard g(c->dev);
     VAMP_CK(c, vamp::launch_refine(c->prm, c->stream));
+    if (c->uni_on) VAMP_CK(c, vamp::launch_union_build(c->prm, c->stream));
     return VAMP_OK;
 }
 
@@ -586,6 +639,7 @@ vamp_status vamp_set_state(vamp_ctx* c, const double* edges, const double* alpha
     if (shift) VAMP_CK(c, cudaMemcpyAsync(c->prm.shift, shift, c->K * 8, cudaMemcpyHostToDevice, c->stream));
     VAMP_CK(c, cudaMemcpyAsync(&c->prm.sc->wmax_gen, &w_max, 8, cudaMemcpyHostToDevice, c->stream));
     VAMP_CK(c, vamp::launch_derive(c->prm, c->stream));
+    if (c->uni_on) VAMP_CK(c, vamp::launch_union_build(c->prm, c->stream));
     VAMP_CK(c, cudaStreamSynchronize(c->stream));
     c->have_pass = 1;
     return VAMP_OK;
@@ -812,14 +866,14 @@ vamp_status vamp_pass_kernel_name(const vamp_ctx* c, int32_t mode, char* buf, in
 vamp_status vamp_pass_kernel_candidates(const vamp_ctx* c, int32_t* count)
 {
     if (!c || !count) return VAMP_ERR_INVALID_ARG;
-    *count = (int32_t)vamp::pass_candidates(c->fp32, c->d, c->n, c->prm.stratified).size();
+    *count = (int32_t)candidates_of(c).size();
     return VAMP_OK;
 }
 
 vamp_status vamp_select_pass_kernel(vamp_ctx* c, int32_t index)
 {
     if (!c) return VAMP_ERR_INVALID_ARG;
-    const std::vector<const PassVariant*> cand = vamp::pass_candidates(c->fp32, c->d, c->n, c->prm.stratified);
+    const std::vector<const PassVariant*> cand = candidates_of(c);
     if (index < 0 || index >= (int32_t)cand.size()) return fail(c, VAMP_ERR_INVALID_ARG, "no such pass-kernel candidate");
     DeviceGuard g(c->dev);
     const vamp_status s = use_variant(c, cand[index]);

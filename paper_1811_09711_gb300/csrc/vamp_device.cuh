@@ -147,7 +147,23 @@ struct Params {
     int n_eq_ent;
     const int32_t* eq_off;   // [K*d + 1]
     const int32_t* eq_ent;   // [n_eq_ent]
+    // interval tables of the FP32-eval union pass (null unless that kernel
+    // is in use; rebuilt whenever the grids change): for coordinate k the
+    // sorted distinct values U_k of every channel's edge images φ_c(ξ_{c,k,j})
+    // (rounded up to FP32), a cell index over them, and for each interval
+    // [U_k[u], U_k[u+1]) the bin densities of all channels (UNION_SLOTS wide)
+    int uMax;          // row stride of uImg / uU / uD: K (n+1)
+    float* uImg;       // [d][K][n+1] edge images per coordinate and channel
+    float* uU;         // [d][uMax] sorted distinct images (first uNU[k] valid)
+    int* uNU;          // [d]
+    uint32_t* uC;      // [d][UNION_CELLS]: count of U_k <= q/L (low 16 bits), values inside the cell (high 16)
+    float* uD;         // [d][uMax][UNION_SLOTS] densities of every channel on each interval
 };
+
+constexpr int UNION_SLOTS = 64;        // channels per density row of the union tables
+constexpr int UNION_LCELLS = 16;       // log2 of the cells per coordinate of the union search
+constexpr int UNION_CELLS = 1 << UNION_LCELLS;
+constexpr int UNION_MAXV = 16384;      // largest K (n+1) the union tables take (16-bit indices, one sort block)
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): 10 rounds of the

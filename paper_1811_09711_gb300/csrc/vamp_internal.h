@@ -55,7 +55,8 @@ struct EvalArgs {
 struct PassVariant {
     int fp32, cpt, D, NB;
     int minb;  // CTAs per SM the kernel is compiled for (register cap), sizes its tile budget
-    const char* family;  // kernel template name ("k_pass")
+    const char* family;  // kernel template name ("k_pass" or "k_union")
+    int uni = 0;         // runs on the union interval tables (vamp_union.cu), not on staged tiles
     const void* fn[2];
     cudaError_t (*launch)(const Params& P, int mode, const PassArgs& A, int grid, size_t smem, cudaStream_t s);
 };
@@ -63,6 +64,17 @@ struct PassVariant {
 void add_pass_variants_f32_generic(std::vector<PassVariant>& v);
 void add_pass_variants_f32_shapes(std::vector<PassVariant>& v);
 void add_pass_variants_f64(std::vector<PassVariant>& v);
+void add_pass_variants_union(std::vector<PassVariant>& v);
+
+// ---- interval tables of the union pass (vamp_union.cu) -----------------------
+// Whether the union kernels take a problem of this kind: FP32-eval,
+// importance sampling, K <= UNION_SLOTS and K (n+1) <= UNION_MAXV.
+bool union_fits(int fp32, int d, int K, int n, int stratified);
+size_t union_bytes(int d, int K, int n);           // device bytes of the tables
+void bind_union(Params& P, unsigned char* base);   // sets P.u* (null: no tables)
+// Rebuilds the tables from P's master grids and lookup blocks (enqueued on s).
+cudaError_t launch_union_build(const Params& P, cudaStream_t s);
+size_t union_pass_smem(const Params& P, const PassVariant& v, int mode);
 
 // Host-side data derived from a vamp_config (vamp_setup.cu).
 struct Setup {
@@ -93,9 +105,10 @@ cudaError_t upload_setup(const Params& P, const Setup& S, cudaStream_t s);
 // (TILE_BUDGET), or `minb` CTAs per SM of the current device.
 void pass_smem(const Params& P, int fp32, int* tile, size_t* smem_int, size_t* smem_gen);
 void pass_smem_for(const Params& P, int fp32, int minb, int* tile, size_t* smem_int, size_t* smem_gen);
-// Candidate kernels for a shape: exact (D, NB) matches first, then generic
-// (generic only for pseudo-stratified problems).
-std::vector<const PassVariant*> pass_candidates(int fp32, int d, int n, int stratified = 0);
+// Candidate kernels for a shape: exact (D, NB) matches first, then generic;
+// with the channel count K given (K > 0) and union_fits, the union kernels
+// after them (exact shape first).
+std::vector<const PassVariant*> pass_candidates(int fp32, int d, int n, int stratified = 0, int K = 0);
 // Raises (never lowers) the dynamic shared-memory limit of a kernel.
 cudaError_t ensure_smem(const void* fn, size_t bytes);
 

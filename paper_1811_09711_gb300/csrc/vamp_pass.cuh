@@ -199,6 +199,61 @@ __device__ __forceinline__ void phase_c_int(const SH& sh, const Calls<T, CPT, SH
     }
 }
 
+// Phase C of a generation batch (chunk `chunk`, calls from `base`): accept iff
+// u w_max < |w| and write the accepted records of the chunk in call order
+// (ballot within a warp, warp offsets through shared memory), then the
+// chunk's count.  Every thread of the CTA takes part.
+template <typename T, int CPT, class SH>
+__device__ __forceinline__ void phase_c_gen(const Params& P, const PassArgs& A, const SH& sh,
+                                            const Calls<T, CPT, SH::DM>& C, int64_t chunk, int64_t base,
+                                            int* wcnt, int* woff, int* round_total, double& wm, bool& bad)
+{
+    constexpr int DM = SH::DM;
+    constexpr int B = PASS_THREADS * CPT;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const double wmax = P.sc->wmax_gen;
+    int running = 0;
+    const int64_t cbase = chunk * B;
+#pragma unroll
+    for (int q = 0; q < CPT; ++q) {
+        double w = 0.0;
+        bool acc = false;
+        if (C.valid[q]) {
+            w = C.g[q] > T(0) ? (double)(C.f[q] / C.g[q]) : 0.0;
+            if (!isfinite(w)) { bad = true; w = 0.0; }
+            wm = fmax(wm, fabs(w));
+            acc = unif64(C.xacc[q]) * wmax < fabs(w);  // the event keeps the sign of w
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, acc);
+        if (lane == 0) wcnt[wid] = __popc(bal);
+        __syncthreads();
+        if (tid == 0) {
+            int s = 0;
+            for (int w2 = 0; w2 < PASS_THREADS / 32; ++w2) { woff[w2] = s; s += wcnt[w2]; }
+            *round_total = s;
+        }
+        __syncthreads();
+        if (acc) {
+            const int pos = running + woff[wid] + __popc(bal & ((1u << lane) - 1u));
+            const int64_t slot = cbase + pos;
+            // record {float p[d]; zero pad to 8 bytes; double w}: 8-byte
+            // stores (records are 8-byte multiples at 8-byte offsets)
+            unsigned char* rec = A.staging + slot * A.rec_bytes;
+            float2* pf2 = reinterpret_cast<float2*>(rec);
+#pragma unroll
+            for (int k = 0; k < DM; k += 2)
+                if (sh.has(k))
+                    pf2[k >> 1] = make_float2((float)C.p[q][k],
+                                              (k + 1 < DM && sh.has(k + 1)) ? (float)C.p[q][k + 1] : 0.0f);
+            *reinterpret_cast<double*>(rec + A.rec_bytes - 8) = w;
+            A.callidx[slot] = (uint32_t)(base + (int64_t)q * PASS_THREADS + tid);
+        }
+        running += *round_total;
+        __syncthreads();
+    }
+    if (tid == 0) A.counts[chunk] = running;
+}
+
 // Flush of a segment: block sums of (s1, s2) and the d-values to global.
 __device__ __forceinline__ void flush_segment(const Params& P, SmemHead& H, int cseg, int dn, double* Ds, double s1,
                                               double s2)
@@ -363,47 +418,7 @@ __global__ void __launch_bounds__(PASS_THREADS, MINB) k_pass(Params P, PassArgs 
                 s1 = s2 = 0.0;
             }
         } else {
-            const double wmax = P.sc->wmax_gen;
-            int running = 0;
-            const int64_t cbase = chunk * B;
-#pragma unroll
-            for (int q = 0; q < CPT; ++q) {
-                double w = 0.0;
-                bool acc = false;
-                if (C.valid[q]) {
-                    w = C.g[q] > T(0) ? (double)(C.f[q] / C.g[q]) : 0.0;
-                    if (!isfinite(w)) { bad = true; w = 0.0; }
-                    wm = fmax(wm, fabs(w));
-                    acc = unif64(C.xacc[q]) * wmax < fabs(w);  // the event keeps the sign of w
-                }
-                const unsigned bal = __ballot_sync(0xffffffffu, acc);
-                if (lane == 0) H.wcnt[wid] = __popc(bal);
-                __syncthreads();
-                if (tid == 0) {
-                    int s = 0;
-                    for (int w2 = 0; w2 < PASS_THREADS / 32; ++w2) { H.woff[w2] = s; s += H.wcnt[w2]; }
-                    H.round_total = s;
-                }
-                __syncthreads();
-                if (acc) {
-                    const int pos = running + H.woff[wid] + __popc(bal & ((1u << lane) - 1u));
-                    const int64_t slot = cbase + pos;
-                    // record {float p[d]; zero pad to 8 bytes; double w}: 8-byte
-                    // stores (records are 8-byte multiples at 8-byte offsets)
-                    unsigned char* rec = A.staging + slot * A.rec_bytes;
-                    float2* pf2 = reinterpret_cast<float2*>(rec);
-#pragma unroll
-                    for (int k = 0; k < DM; k += 2)
-                        if (sh.has(k))
-                            pf2[k >> 1] = make_float2((float)C.p[q][k],
-                                                      (k + 1 < DM && sh.has(k + 1)) ? (float)C.p[q][k + 1] : 0.0f);
-                    *reinterpret_cast<double*>(rec + A.rec_bytes - 8) = w;
-                    A.callidx[slot] = (uint32_t)(base + (int64_t)q * PASS_THREADS + tid);
-                }
-                running += H.round_total;
-                __syncthreads();
-            }
-            if (tid == 0) A.counts[chunk] = running;
+            phase_c_gen<T, CPT>(P, A, sh, C, chunk, base, H.wcnt, H.woff, &H.round_total, wm, bad);
             chunk += gridDim.x;
         }
     }

@@ -330,7 +330,7 @@ void pass_smem_for(const Params& P, int fp32, int minb, int* tile, size_t* smem_
     smem_for_budget(P, fp32, budget, tile, smem_int, smem_gen);
 }
 
-std::vector<const PassVariant*> pass_candidates(int fp32, int d, int n, int stratified)
+std::vector<const PassVariant*> pass_candidates(int fp32, int d, int n, int stratified, int K)
 {
     static std::vector<PassVariant> all;
     static std::once_flag once;
@@ -338,14 +338,24 @@ std::vector<const PassVariant*> pass_candidates(int fp32, int d, int n, int stra
         add_pass_variants_f32_generic(all);
         add_pass_variants_f32_shapes(all);
         add_pass_variants_f64(all);
+        add_pass_variants_union(all);
     });
-    std::vector<const PassVariant*> exact, generic;
+    const bool uni = K > 0 && union_fits(fp32, d, K, n, stratified);
+    std::vector<const PassVariant*> exact, generic, uexact, ugeneric;
     for (const PassVariant& v : all) {
         if (v.fp32 != fp32) continue;
+        if (v.uni) {
+            if (!uni) continue;
+            if (v.D == d && v.NB == n) uexact.push_back(&v);
+            else if (v.D == 0 && v.NB == 0) ugeneric.push_back(&v);
+            continue;
+        }
         if (v.D == d && v.NB == n && !stratified) exact.push_back(&v);
         else if (v.D == 0 && v.NB == 0) generic.push_back(&v);
     }
     for (const PassVariant* v : generic) exact.push_back(v);
+    for (const PassVariant* v : uexact) exact.push_back(v);
+    for (const PassVariant* v : ugeneric) exact.push_back(v);
     return exact;
 }
 

@@ -1,0 +1,310 @@
+// vamp_union.cuh -- the FP32-eval pass kernel over per-coordinate interval
+// tables ("union pass"), for problems with at most UNION_SLOTS channels.
+//
+// g(p) (Eq. 30) needs, for every channel c and coordinate k, the density of
+// the bin of grid row (c, k) that holds x_{c,k} = φ_c^{-1}(p)_k.  The maps
+// are increasing on [0, 1], so that bin is also the one whose image
+// [φ_c(ξ_j), φ_c(ξ_{j+1})) holds p_k.  After every grid change the tables
+// (vamp_union.cu) merge the images of all channels' edges on coordinate k
+// into one sorted list U_k (rounded up to FP32, so that p >= U decides
+// exactly as p >= φ_c(ξ_j) for an FP32 p); between two neighbouring values
+// of U_k every channel's bin is fixed.  One interval search per coordinate
+// then gives the K densities of a call as one 256-byte row, read coalesced.
+// Only the Jacobians of the mapped coordinates remain per channel, and they
+// need no inverse map: 1/φ' at p is Γ/(A((p-m)² + Γ²)) for a Breit-Wigner
+// map and p^(-4/5)/5 for the power map x^5.
+//
+// Per batch of PASS_THREADS calls (one per thread), as k_pass where not said:
+//   A  Philox words, channel, forward map, own term, integrand;
+//   S  interval u_k of p_k on every coordinate (cell entry, short scan);
+//   J  per channel c: α_c × the Jacobians of its mapped coordinates at p
+//      (0 for the own and for switched-off channels) into shared memory, and
+//      the matching integrand peak;
+//   U  per warp, its 32 calls transposed: lane l multiplies the densities of
+//      channels 2l, 2l+1 on every coordinate (one float2 of the call's row)
+//      into the factors of J; a reduce-scatter over the lanes leaves
+//      Σ_c α_c g_c/φ'_c of call i in lane i;
+//   C  weights, sums, d-values (integration) or acceptance (generation).
+#pragma once
+
+#include "vamp_pass.cuh"
+
+namespace vamp {
+
+constexpr int UNION_JSTR = UNION_SLOTS + 2;  // floats per call row of the channel factors (8-byte rows, 2-way banks)
+
+// A channel's terms for part J, copied into shared memory once per CTA:
+// α_c, the matching peak's weight, and per mapped slot its coordinate k,
+// map kind and constants (Breit-Wigner: m, Γ², Γ/A; power: δ, 1/powN).
+struct UnionChan {
+    float alpha, wz;
+    int nslot, pad;
+    float4 slot[MAXMAP];  // {c0, c1, c2, bits of (k | kind << 8)}
+};
+static_assert(sizeof(UnionChan) == 80, "UnionChan layout");
+
+// Shared-memory layout of the union kernel (bytes from the start).
+struct UnionSmem {
+    int ds, js, ps, us, ch, bytes;
+};
+__host__ __device__ constexpr int union_pstride(int DM) { return DM | 1; }
+__host__ __device__ constexpr UnionSmem union_smem_layout(int DM, int d, int n, int mode)
+{
+    const int nw = PASS_THREADS / 32;
+    const int ds = SMEM_HEAD;
+    const int js = ds + (mode == 0 ? round_up(d * n * 8, 16) : 0);
+    const int ps = js + nw * 32 * UNION_JSTR * 4;
+    const int us = ps + round_up(PASS_THREADS * union_pstride(DM) * 4, 16);
+    const int ch = us + round_up(nw * DM * 32 * 2, 16);
+    const int bytes = ch + UNION_SLOTS * (int)sizeof(UnionChan);
+    return UnionSmem{ds, js, ps, us, ch, bytes};
+}
+
+// One float2 of a density row, read through L1 without allocating there (the
+// rows stream past once per call; L1 keeps the lookup blocks and search
+// cells instead).
+__device__ __forceinline__ float2 ld_row(const float2* p)
+{
+    float2 v;
+    asm("ld.global.nc.L1::no_allocate.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
+    return v;
+}
+
+// Interval of x in U_k: the index of the largest U_k[u] <= x (0 if none).
+__device__ __forceinline__ int union_interval(const Params& P, int k, float x)
+{
+    const int q = min(Prec<float>::cell(x, UNION_LCELLS), UNION_CELLS - 1);
+    const uint32_t e = __ldg(P.uC + (size_t)k * UNION_CELLS + q);
+    const int base = (int)(e & 0xffffu), span = (int)(e >> 16);
+    const float* Uk = P.uU + (size_t)k * P.uMax + base;
+    int t = 0;
+    while (t < span && __ldg(Uk + t) <= x) ++t;
+    return max(base + t - 1, 0);
+}
+
+template <int MODE, int D_, int NB_, int MINB>
+__global__ void __launch_bounds__(PASS_THREADS, MINB) k_union(Params P, PassArgs A)
+{
+    using SH = Shape<float, D_, NB_>;
+    constexpr int DM = SH::DM;
+    constexpr int PSTR = union_pstride(DM);
+    constexpr int NW = PASS_THREADS / 32;
+    extern __shared__ __align__(128) unsigned char smem[];
+    SmemHead& H = *reinterpret_cast<SmemHead*>(smem);
+    const SH sh(P.lay32, P.d, P.n);
+    const int d = sh.d(), n = sh.n(), dn = d * n, K = P.K;
+    const UnionSmem L = union_smem_layout(DM, d, n, MODE);
+    double* Ds = reinterpret_cast<double*>(smem + L.ds);
+    float* Js = reinterpret_cast<float*>(smem + L.js);
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    float* Jw = Js + wid * 32 * UNION_JSTR;                                       // factors of this warp's calls
+    float* Pt = reinterpret_cast<float*>(smem + L.ps) + tid * PSTR;                // p of this thread's call
+    uint16_t* Uw = reinterpret_cast<uint16_t*>(smem + L.us) + wid * DM * 32;     // intervals of the warp's calls
+    constexpr int B = PASS_THREADS;
+
+    UnionChan* ucs = reinterpret_cast<UnionChan*>(smem + L.ch);
+    // channel slots >= K keep factor 0 (their density rows are 0 as well)
+    for (int i = tid; i < NW * 32 * UNION_JSTR; i += PASS_THREADS) Js[i] = 0.f;
+    // part J's channel terms from the lookup-block headers (slot s of channel
+    // c by thread 4c + s)
+    for (int t = tid; t < K * MAXMAP; t += PASS_THREADS) {
+        const int c = t / MAXMAP, s = t % MAXMAP;
+        const ChanHdr<float>* h = reinterpret_cast<const ChanHdr<float>*>(P.lk32 + (size_t)c * sh.bytes());
+        const uint32_t mask = h->mask;
+        const uint64_t slotpack = h->slotpack;
+        if (s == 0) {
+            ucs[c].alpha = P.alpha32[c];
+            ucs[c].wz = h->wz;
+            ucs[c].nslot = __popc(mask);
+        }
+        for (uint32_t m = mask; m; m &= m - 1u) {
+            const int k = __ffs(m) - 1;
+            if ((int)((slotpack >> (4 * k)) & 0xFu) != s) continue;
+            const int kind = (h->kinds >> (8 * s)) & 0xff;
+            const float* sp = h->sp[s];
+            float4 r;
+            if (kind == MAP_BW) r = make_float4(sp[SP_M], sp[SP_G2], sp[SP_GINVA], 0.f);
+            else r = make_float4(sp[SP_DEL], sp[SP_INVPOWN], 0.f, 0.f);
+            r.w = __int_as_float(k | (kind << 8));
+            ucs[c].slot[s] = r;
+        }
+    }
+    __syncthreads();
+
+    // ---- work of this CTA (as k_pass, one call per thread) -------------------
+    int64_t r0 = 0, r1 = 0, nbatch = 0;
+    if (MODE == 0) {
+        const int64_t N = P.sc->n_total;
+        r0 = N * blockIdx.x / gridDim.x;
+        r1 = N * (blockIdx.x + 1) / gridDim.x;
+        for (int64_t i = r0; i < r1;) {
+            const int c = find_channel(P.Pc, K, i);
+            const int64_t e = min(r1, P.Pc[c + 1]);
+            nbatch += (e - i + B - 1) / B;
+            i = e;
+        }
+    } else {
+        const int64_t nch = A.nchunks;
+        nbatch = blockIdx.x < nch ? (nch - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    }
+    if (nbatch == 0) return;
+
+    double wm = 0.0, s1 = 0.0, s2 = 0.0;
+    bool bad = false;
+    int64_t i0 = r0;
+    int cseg = -1;
+    int64_t seg_end = 0;
+    double sft = 0.0;
+    int64_t chunk = blockIdx.x;
+    const float gc = P.gcen_f, k2 = P.gk2_f;
+    const bool with_f = P.matching != 0;
+
+    for (int64_t bt = 0; bt < nbatch; ++bt) {
+        int64_t base, end;
+        if (MODE == 0) {
+            if (i0 >= seg_end || cseg < 0) {
+                cseg = find_channel(P.Pc, K, i0);
+                seg_end = min(r1, P.Pc[cseg + 1]);
+                sft = P.shift[cseg];
+                for (int q = tid; q < dn; q += PASS_THREADS) Ds[q] = 0.0;
+                s1 = s2 = 0.0;
+                __syncthreads();
+            }
+            base = i0;
+            end = min(seg_end, i0 + B);
+        } else {
+            base = chunk * B;
+            end = min(A.batch, base + B);
+        }
+
+        // ---- A: own channel's forward map, own term, integrand ------------------
+        Calls<float, 1, DM> C;
+        phase_a<float, MODE, 1>(P, sh, A.field, base, end, cseg, C);
+
+        // ---- S: p to shared memory and its interval on every coordinate --------
+#pragma unroll
+        for (int k = 0; k < DM; ++k)
+            if (sh.has(k)) Pt[k] = C.p[0][k];
+#pragma unroll
+        for (int k = 0; k < DM; ++k)
+            if (sh.has(k)) Uw[k * 32 + lane] = (uint16_t)union_interval(P, k, C.p[0][k]);
+
+        // ---- J: α_c times the Jacobians of channel c's mapped coordinates ------
+        const int own = MODE == 0 ? cseg : C.cq[0];
+        const float Aq = C.Aexp[0];
+        float f = C.f[0];
+#pragma unroll 2
+        for (int c2 = 0; c2 < K; ++c2) {
+            const UnionChan& ch = ucs[c2];
+            const int ns = ch.nslot;
+            float J = 1.f, F = 1.f, as = 0.f;
+#pragma unroll
+            for (int s = 0; s < MAXMAP; ++s) {
+                if (s < ns) {
+                    const float4 r = ch.slot[s];
+                    const int kb = __float_as_int(r.w);
+                    const float pk = Pt[kb & 0xff];
+                    if ((kb >> 8) == MAP_BW) {
+                        const float dp = pk - r.x;
+                        const float jfac = Prec<float>::div(r.z, fmaf(dp, dp, r.y));
+                        J *= jfac;
+                        F *= jfac;
+                    } else if ((kb >> 8) == MAP_POW) {
+                        J *= 0.2f * Prec<float>::powm08(pk);  // 1/φ' = 1/(5 x^4) with x = p^(1/5)
+                        if (with_f) F *= Prec<float>::powm08(pk + r.x) * r.y;
+                    }
+                    const float u = pk - gc;
+                    as += u * u * k2;
+                }
+            }
+            const float a = ch.alpha;
+            Jw[lane * UNION_JSTR + c2] = (a != 0.f && c2 != own) ? a * J : 0.f;
+            if (with_f) f += ch.wz * Prec<float>::exp2_(as - Aq) * F;
+        }
+        __syncwarp();
+
+        // ---- U: densities of the warp's calls, channels 2l and 2l+1 in lane l --
+        {
+            float2 acc[32];
+#pragma unroll
+            for (int i = 0; i < 32; ++i) acc[i] = *reinterpret_cast<const float2*>(Jw + i * UNION_JSTR + 2 * lane);
+#pragma unroll 1
+            for (int k = 0; k < d; ++k) {
+                const float2* row = reinterpret_cast<const float2*>(P.uD + (size_t)k * P.uMax * UNION_SLOTS) + lane;
+                const uint16_t* uk = Uw + k * 32;
+#pragma unroll
+                for (int i = 0; i < 32; ++i) {
+                    const float2 v = ld_row(row + (size_t)uk[i] * (UNION_SLOTS / 2));
+                    acc[i].x *= v.x;
+                    acc[i].y *= v.y;
+                }
+            }
+            float v[32];
+#pragma unroll
+            for (int i = 0; i < 32; ++i) v[i] = acc[i].x + acc[i].y;
+            // reduce-scatter: in the step of width s each lane trades half of
+            // its partial sums with lane ^ s (the lane with bit s set keeps
+            // the upper half), so that after five steps v[0] is the sum over
+            // all lanes for call `lane`
+#pragma unroll
+            for (int s = 16; s >= 1; s >>= 1) {
+                const bool up = (lane & s) != 0;
+#pragma unroll
+                for (int j = 0; j < s; ++j) {
+                    const float send = up ? v[j] : v[j + s];
+                    const float keep = up ? v[j + s] : v[j];
+                    v[j] = keep + __shfl_xor_sync(0xffffffffu, send, s);
+                }
+            }
+            C.g[0] += v[0];
+        }
+        C.f[0] = f;
+#pragma unroll
+        for (int k = 0; k < DM; ++k)
+            if (sh.has(k)) C.p[0][k] = Pt[k];
+        __syncwarp();  // the next batch overwrites this warp's factors and intervals
+
+        // ---- C: weights and accumulation ----------------------------------------
+        if (MODE == 0) {
+            phase_c_int<float, 1>(sh, C, sft, Ds, s1, s2, wm, bad);
+            i0 = end;
+            if (i0 >= seg_end) {
+                flush_segment(P, H, cseg, dn, Ds, s1, s2);
+                s1 = s2 = 0.0;
+            }
+        } else {
+            phase_c_gen<float, 1>(P, A, sh, C, chunk, base, H.wcnt, H.woff, &H.round_total, wm, bad);
+            chunk += gridDim.x;
+        }
+    }
+
+    if (bad) atomicOr(&P.sc->err, ERR_NONFINITE);
+    block_max_to(H, wm, MODE == 0 ? &P.sc->wmax_bits : &P.sc->gen_bmax_bits);
+}
+
+template <int D_, int NB_, int MINB>
+cudaError_t union_launch_t(const Params& P, int mode, const PassArgs& A, int grid, size_t smem, cudaStream_t s)
+{
+    if (mode) k_union<1, D_, NB_, MINB><<<grid, PASS_THREADS, smem, s>>>(P, A);
+    else k_union<0, D_, NB_, MINB><<<grid, PASS_THREADS, smem, s>>>(P, A);
+    return cudaGetLastError();
+}
+
+template <int D_, int NB_, int MINB = 2>
+PassVariant make_union_variant()
+{
+    PassVariant v;
+    v.fp32 = 1;
+    v.cpt = 1;
+    v.D = D_;
+    v.NB = NB_;
+    v.minb = MINB;
+    v.family = "k_union";
+    v.uni = 1;
+    v.fn[0] = (const void*)k_union<0, D_, NB_, MINB>;
+    v.fn[1] = (const void*)k_union<1, D_, NB_, MINB>;
+    v.launch = &union_launch_t<D_, NB_, MINB>;
+    return v;
+}
+
+}  // namespace vamp

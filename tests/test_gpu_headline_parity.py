@@ -5,9 +5,11 @@ oracle adapted over four iterations of 1e6 calls.
 
 Every compiled pass kernel that can run this shape is pinned in turn
 (vamp_select_pass_kernel) and its name asserted, so the shape-specialised
-kernels the autotuner picks for the benchmark -- their tiling, slow-row
-mask, single-probe lookups and lane-rotated d-value atomics -- are compared
-with the oracle bin by bin, not only through the pass integral:
+kernels the autotuner picks for the benchmark -- the staged-tile k_pass
+(tiling, slow-row mask, single-probe lookups, lane-rotated d-value atomics)
+and the k_union pass over per-coordinate interval tables (edge images,
+interval search, transposed density rows) -- are compared with the oracle
+bin by bin, not only through the pass integral:
 
   * call allocation N_c (Eq. 23 with R6): bit-exact;
   * per-bin d-values D_{c,k,j} (Eq. 15), per-channel I_c, V_c, w_max, the
@@ -191,8 +193,10 @@ def test_fp32_kernels_elementwise(V, ref):
         assert redge < EDGE_TOL, name
         assert ralpha < ALPHA_TOL, name
     names = [x[0] for x in runs]
-    # the benchmark's kernel is among those compared
+    # the benchmark's kernels are among those compared: the staged-tile pass
+    # and the pass over per-coordinate interval tables
     assert "k_pass<float, 0, 2, 14, 100, 2>" in names, names
+    assert "k_union<float, 0, 1, 14, 100, 2>" in names, names
     assert len(names) == len(set(names)) == ncand
     # same family, same per-call arithmetic: sums agree to FP64 summation order
     generic = {nm.split("<")[0]: x for x in runs for nm in [x[0]] if nm.endswith(", 0, 0, 2>")}
