@@ -144,12 +144,26 @@ def job_throughput(t_ms: float, calls: float, world_size: int, device="cpu"):
     return float(mx[0]), float(sm[1])
 
 
-KERNEL_SOURCES = ["vamp_pass.cuh", "vamp_device.cuh", "vamp_pass_f32_shapes.cu", "vamp_internal.h"]
+# per kernel family: the sources its traffic record is bound to and the
+# committed ncu summary that holds the record
+KERNEL_SOURCES = {
+    "k_pass": (["vamp_pass.cuh", "vamp_device.cuh", "vamp_pass_f32_shapes.cu", "vamp_internal.h"],
+               "k_pass_fp32_collider_d14_k64.md"),
+    "k_union": (["vamp_union.cuh", "vamp_pass.cuh", "vamp_device.cuh", "vamp_union.cu", "vamp_internal.h"],
+                "k_union_fp32_collider_d14_k64.md"),
+}
 
 
 # kernels of one timed adaptation step: allocation, sampling pass, pass
-# result, result copy (asynchronous form), rebinning, channel weights
+# result, result copy (asynchronous form), rebinning, channel weights; the
+# union pass adds the four kernels that rebuild its interval tables after
+# the rebinning (edge images, sort, cell index, density rows)
 KERNELS_PER_STEP = 6
+UNION_BUILD_KERNELS = 4
+
+
+def kernel_family(kernel: str) -> str:
+    return kernel.split("<")[0]
 
 
 def measured_traffic(kernel: str):
@@ -157,12 +171,15 @@ def measured_traffic(kernel: str):
     None when the kernel sources changed since the counters were taken."""
     import hashlib
     import re
+    fam = KERNEL_SOURCES.get(kernel_family(kernel))
+    if fam is None:
+        return None
     h = hashlib.sha256()
-    for s in KERNEL_SOURCES:
+    for s in fam[0]:
         with open(os.path.join(ROOT, "paper_1811_09711_gb300", "csrc", s), "rb") as f:
             h.update(f.read())
     try:
-        with open(os.path.join(ROOT, "profiles", "k_pass_fp32_collider_d14_k64.md")) as f:
+        with open(os.path.join(ROOT, "profiles", fam[1])) as f:
             txt = f.read()
     except OSError:
         return None
@@ -233,6 +250,34 @@ def fp64_ops_per_call(pr) -> float:
     square, the shifted sums (difference, sum, multiply-add), the maximum,
     and one d-value addition per coordinate."""
     return 6.0 + pr.d
+
+
+def union_l2_bytes_per_call(pr) -> float:
+    """Bytes the union pass reads from L2 per call: one 256-byte density row
+    (UNION_SLOTS = 64 channels, FP32) and one 4-byte cell entry per
+    coordinate (the scans past the cell entry are rare and not counted)."""
+    return pr.d * (64 * 4 + 4.0)
+
+
+def union_xu_ops_per_call(pr) -> float:
+    """MUFU operations of one call in the union pass: one exp2 per channel
+    (its peak's Gaussian factor); one reciprocal per Breit-Wigner coordinate
+    (the Jacobian at p); two log2 and two exp2 per power-law coordinate
+    (p^-0.8 for the Jacobian, (p + δ)^-0.8 for the peak).  No inverse maps."""
+    bw, pw = mapped_kinds(pr)
+    return float(pr.n_channels + bw + 4 * pw)
+
+
+def union_lsu_wavefronts_per_call(pr) -> float:
+    """Shared-memory wavefronts of one call in the union pass at one per warp
+    access: per channel its record and per mapped coordinate the slot record
+    and the call's coordinate (part J, per thread); per coordinate the
+    interval broadcast of part U; the channel factors written (two
+    wavefronts per warp store of 32 calls) and read back (two per float2
+    warp load)."""
+    mapped = int(sum(int(x) for x in pr.channels.n_mapped))
+    K = pr.n_channels
+    return (K + 2.0 * mapped) / 32.0 + pr.d + 2.0 * K / 32.0 + 2.0
 
 
 def fp64_form_ops_per_call(pr) -> float:
@@ -589,27 +634,36 @@ def run_gpu(args):
     mp = V.measure_peaks()
     k_ms = ks["sample_ms"] / max(ks["sample_launches"], 1)
     kcalls = calls / max(args.steps, 1) / (k_ms / 1e3)  # calls/s of the pass kernel
+    kname = g.kernel_name()
+    union = kernel_family(kname) == "k_union"
     work = {"alu": (algorithmic_ops_per_call(pr), mp["fp32_lane_ops"], "Tops/s",
-                    "32-bit lane-operations (FP32 and integer) per call"),
-            "lsu": (lsu_wavefronts_per_call(pr), mp["lds_wavefronts"], "Twavefronts/s",
-                    "shared-memory load wavefronts per call (three 4-byte reads per lookup, 32 lanes each)"),
-            "xu": (xu_ops_per_call(pr), mp["xu_lane_ops"], "Tops/s", "MUFU operations per call"),
-            "fp64": (fp64_ops_per_call(pr), mp["fp64_lane_ops"], "Tops/s", "FP64 operations per call")}
+                    "32-bit lane-operations (FP32 and integer) per call: the method's work, as for every kernel")}
+    if union:
+        work["l2"] = (union_l2_bytes_per_call(pr), mp["l2_read_bytes"], "TB/s",
+                      "bytes read from L2 per call (a 256-byte density row and a cell entry per coordinate)")
+        work["lsu"] = (union_lsu_wavefronts_per_call(pr), mp["lds_wavefronts"], "Twavefronts/s",
+                       "shared-memory wavefronts per call (channel records, coordinates, interval broadcasts, "
+                       "channel factors)")
+        work["xu"] = (union_xu_ops_per_call(pr), mp["xu_lane_ops"], "Tops/s", "MUFU operations per call")
+    else:
+        work["lsu"] = (lsu_wavefronts_per_call(pr), mp["lds_wavefronts"], "Twavefronts/s",
+                       "shared-memory load wavefronts per call (three 4-byte reads per lookup, 32 lanes each)")
+        work["xu"] = (xu_ops_per_call(pr), mp["xu_lane_ops"], "Tops/s", "MUFU operations per call")
+    work["fp64"] = (fp64_ops_per_call(pr), mp["fp64_lane_ops"], "Tops/s", "FP64 operations per call")
     pipes = {}
     for name, (per_call, peak, unit, what) in work.items():
         ach = per_call * kcalls
         pipes[name] = {"achieved": ach / 1e12, "peak": peak / 1e12, "unit": unit, "frac": ach / peak,
                        "per_call": per_call, "work": what}
     bound = max(pipes, key=lambda k: pipes[k]["frac"])
-    kname = g.kernel_name()
     bp = pipes[bound]
     roof = {"bound": bound, "achieved": bp["achieved"], "peak": bp["peak"], "unit": bp["unit"],
             "frac": bp["frac"], "traffic": measured_traffic(kname),
             "kernel": kname, "kernel_ms": k_ms, "ops_per_call": algorithmic_ops_per_call(pr),
             "frac_lookups_only": lookup_ops_per_call(pr) * kcalls / mp["fp32_lane_ops"],
             "pipes": pipes,
-            "peak_source": "measured on this GPU by vamp_measure_peaks (FFMA, DFMA, MUFU and conflict-free "
-                           "shared-load kernels)"}
+            "peak_source": "measured on this GPU by vamp_measure_peaks (FFMA, DFMA, MUFU, conflict-free "
+                           "shared-load and L2-read kernels)"}
     if batch is not None:
         for tag in ("tuned", "fixed"):
             batch[tag]["frac_of_alu_peak"] = batch[tag]["alu_ops_per_s"] / mp["fp32_lane_ops"]
@@ -642,7 +696,8 @@ def run_gpu(args):
            "last_pass": {"integral": last.integral, "sigma": math.sqrt(max(last.variance, 0.0)),
                          "efficiency": last.efficiency, "combined": last.combined,
                          "combined_sigma": last.combined_sigma, "chi2_dof": last.chi2_dof},
-           "e2e": e2e, "gpu_launches": KERNELS_PER_STEP * args.steps, "roofline": roof, "clocks": clk}
+           "e2e": e2e, "gpu_launches": (KERNELS_PER_STEP + (UNION_BUILD_KERNELS if union else 0)) * args.steps,
+           "roofline": roof, "clocks": clk}
     if batch is not None:
         res["batch"] = batch
     if serving is not None:

@@ -293,15 +293,17 @@ vamp_status vamp_pass_kernel_info(const vamp_ctx *ctx, int32_t *fp32, int32_t *c
  * no counterpart).  Per second, summed over all SMs: FP32 fused
  * multiply-add lane-instructions (the issue rate of 32-bit arithmetic),
  * FP64 fused multiply-add lane-instructions, MUFU (special-function unit)
- * lane-instructions (2^x), and shared-memory load wavefronts (one per warp
- * load of 32 consecutive words).  Runs on the current device and
- * synchronises it; takes a few tens of milliseconds.  OOM / CUDA on
- * failure. */
+ * lane-instructions (2^x), shared-memory load wavefronts (one per warp
+ * load of 32 consecutive words), and bytes read from L2 by coalesced
+ * 16-byte loads that bypass L1 (a 32 MiB buffer resident in L2).  Runs on
+ * the current device and synchronises it; takes a few tens of
+ * milliseconds.  OOM / CUDA on failure. */
 typedef struct vamp_pipe_peaks {
     double fp32_lane_ops;
     double fp64_lane_ops;
     double xu_lane_ops;
     double lds_wavefronts;
+    double l2_read_bytes;
 } vamp_pipe_peaks;
 vamp_status vamp_measure_peaks(vamp_pipe_peaks *out);
 

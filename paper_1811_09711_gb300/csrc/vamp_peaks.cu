@@ -1,7 +1,7 @@
 // vamp_peaks.cu -- vamp_measure_peaks: the per-pipe throughput of this GPU
 // measured with small kernels, the denominators of the benchmark's
-// per-pipe roofline (FP32 lanes, FP64 lanes, the MUFU special-function unit
-// and shared-memory load wavefronts).
+// per-pipe roofline (FP32 lanes, FP64 lanes, the MUFU special-function unit,
+// shared-memory load wavefronts and L2 reads).
 //
 // Each kernel runs enough independent dependency chains per thread to keep
 // its pipe busy, over a grid of every SM's resident CTAs, and is timed with
@@ -93,6 +93,34 @@ __global__ void __launch_bounds__(PK_THREADS) k_peak_lds(unsigned* out, int iter
     out[blockIdx.x * PK_THREADS + threadIdx.x] = t;
 }
 
+// L2 reads: coalesced 16-byte loads over a buffer that stays in L2 (the
+// loads do not allocate in L1), PK_CHAINS independent loads per step
+constexpr int PK_L2_LOG4 = 21;  // 2^21 float4 = 32 MiB
+__device__ __forceinline__ float4 ld_l2(const float4* p)
+{
+    float4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "l"(p));
+    return v;
+}
+__global__ void __launch_bounds__(PK_THREADS) k_peak_l2(const float4* buf, float* out, int iters)
+{
+    const unsigned mask = (1u << PK_L2_LOG4) - 1u;
+    const unsigned nt = gridDim.x * PK_THREADS;
+    unsigned i = blockIdx.x * PK_THREADS + threadIdx.x;
+    float s = 0.f;
+    for (int r = 0; r < iters; ++r) {
+        float4 v[PK_CHAINS];
+#pragma unroll
+        for (int c = 0; c < PK_CHAINS; ++c) v[c] = ld_l2(buf + ((i + c * nt) & mask));
+#pragma unroll
+        for (int c = 0; c < PK_CHAINS; ++c) s += (v[c].x + v[c].y) + (v[c].z + v[c].w);
+        i += PK_CHAINS * nt;
+    }
+    out[blockIdx.x * PK_THREADS + threadIdx.x] = s;
+}
+
 template <typename F>
 cudaError_t time_kernel(F launch, float* ms)
 {
@@ -121,17 +149,23 @@ extern "C" vamp_status vamp_measure_peaks(vamp_pipe_peaks* out)
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return VAMP_ERR_CUDA;
-    int bf = 0, bd = 0, bm = 0, bl = 0;
+    int bf = 0, bd = 0, bm = 0, bl = 0, b2 = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bf, k_peak_ffma, PK_THREADS, 0) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bd, k_peak_dfma, PK_THREADS, 0) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bm, k_peak_mufu, PK_THREADS, 0) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bl, k_peak_lds, PK_THREADS, 0) != cudaSuccess)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bl, k_peak_lds, PK_THREADS, 0) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, k_peak_l2, PK_THREADS, 0) != cudaSuccess)
         return VAMP_ERR_CUDA;
     const int grid = sms * (bf > 0 ? bf : 1);
     const int gd = sms * (bd > 0 ? bd : 1), gm = sms * (bm > 0 ? bm : 1), gl = sms * (bl > 0 ? bl : 1);
-    const int maxg = grid > gd ? (grid > gm ? (grid > gl ? grid : gl) : (gm > gl ? gm : gl)) : (gd > gm ? (gd > gl ? gd : gl) : (gm > gl ? gm : gl));
+    const int g2 = sms * (b2 > 0 ? b2 : 1);
+    int maxg = grid;
+    for (int g : {gd, gm, gl, g2}) maxg = g > maxg ? g : maxg;
     void* buf = nullptr;
     if (cudaMalloc(&buf, (size_t)maxg * PK_THREADS * 8) != cudaSuccess) return VAMP_ERR_OOM;
+    void* l2buf = nullptr;
+    const size_t l2bytes = (size_t)16 << PK_L2_LOG4;
+    if (cudaMalloc(&l2buf, l2bytes) != cudaSuccess) { cudaFree(buf); return VAMP_ERR_OOM; }
     vamp_status st = VAMP_OK;
     float ms = 0.f;
     const int it_f = 1 << 16, it_d = 1 << 12, it_m = 1 << 13, it_l = 1 << 14;
@@ -144,7 +178,13 @@ extern "C" vamp_status vamp_measure_peaks(vamp_pipe_peaks* out)
     if (e == cudaSuccess) out->xu_lane_ops = (double)gm * PK_THREADS * PK_CHAINS * it_m / (ms * 1e-3);
     if (e == cudaSuccess) e = time_kernel([&] { k_peak_lds<<<gl, PK_THREADS>>>((unsigned*)buf, it_l); }, &ms);
     if (e == cudaSuccess) out->lds_wavefronts = (double)gl * (PK_THREADS / 32) * PK_CHAINS * it_l / (ms * 1e-3);
+    const int it_2 = 1 << 9;
+    if (e == cudaSuccess) e = cudaMemset(l2buf, 0, l2bytes);
+    if (e == cudaSuccess)
+        e = time_kernel([&] { k_peak_l2<<<g2, PK_THREADS>>>((const float4*)l2buf, (float*)buf, it_2); }, &ms);
+    if (e == cudaSuccess) out->l2_read_bytes = (double)g2 * PK_THREADS * PK_CHAINS * it_2 * 16.0 / (ms * 1e-3);
     if (e != cudaSuccess) st = VAMP_ERR_CUDA;
     cudaFree(buf);
+    cudaFree(l2buf);
     return st;
 }

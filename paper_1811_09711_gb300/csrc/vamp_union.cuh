@@ -34,12 +34,14 @@ namespace vamp {
 constexpr int UNION_JSTR = UNION_SLOTS + 2;  // floats per call row of the channel factors (8-byte rows, 2-way banks)
 
 // A channel's terms for part J, copied into shared memory once per CTA:
-// α_c, the matching peak's weight, and per mapped slot its coordinate k,
-// map kind and constants (Breit-Wigner: m, Γ², Γ/A; power: δ, 1/powN).
+// α_c, the matching peak's weight, and its mapped coordinates, the nbw
+// Breit-Wigner ones first (m, Γ², Γ/A, k), then the npw power-law ones
+// (δ, 1/powN, 0, k), so that part J runs two loops of uniform trip count
+// with no test of the map kind.
 struct UnionChan {
     float alpha, wz;
-    int nslot, pad;
-    float4 slot[MAXMAP];  // {c0, c1, c2, bits of (k | kind << 8)}
+    int nbw, npw;
+    float4 slot[MAXMAP];  // {c0, c1, c2, bits of k}
 };
 static_assert(sizeof(UnionChan) == 80, "UnionChan layout");
 
@@ -70,11 +72,17 @@ __device__ __forceinline__ float2 ld_row(const float2* p)
     return v;
 }
 
-// Interval of x in U_k: the index of the largest U_k[u] <= x (0 if none).
-__device__ __forceinline__ int union_interval(const Params& P, int k, float x)
+// Cell entry of x on coordinate k (the first step of union_interval).
+__device__ __forceinline__ uint32_t union_cell_entry(const Params& P, int k, float x)
 {
     const int q = min(Prec<float>::cell(x, UNION_LCELLS), UNION_CELLS - 1);
-    const uint32_t e = __ldg(P.uC + (size_t)k * UNION_CELLS + q);
+    return __ldg(P.uC + (size_t)k * UNION_CELLS + q);
+}
+
+// Interval of x in U_k from x's cell entry e: the index of the largest
+// U_k[u] <= x (0 if none).
+__device__ __forceinline__ int union_interval(const Params& P, int k, float x, uint32_t e)
+{
     const int base = (int)(e & 0xffffu), span = (int)(e >> 16);
     const float* Uk = P.uU + (size_t)k * P.uMax + base;
     int t = 0;
@@ -105,29 +113,29 @@ __global__ void __launch_bounds__(PASS_THREADS, MINB) k_union(Params P, PassArgs
     UnionChan* ucs = reinterpret_cast<UnionChan*>(smem + L.ch);
     // channel slots >= K keep factor 0 (their density rows are 0 as well)
     for (int i = tid; i < NW * 32 * UNION_JSTR; i += PASS_THREADS) Js[i] = 0.f;
-    // part J's channel terms from the lookup-block headers (slot s of channel
-    // c by thread 4c + s)
-    for (int t = tid; t < K * MAXMAP; t += PASS_THREADS) {
-        const int c = t / MAXMAP, s = t % MAXMAP;
+    // part J's channel terms from the lookup-block headers (one thread per
+    // channel; mapped coordinates of other kinds carry no factor)
+    for (int c = tid; c < K; c += PASS_THREADS) {
         const ChanHdr<float>* h = reinterpret_cast<const ChanHdr<float>*>(P.lk32 + (size_t)c * sh.bytes());
-        const uint32_t mask = h->mask;
+        const uint32_t mask = h->mask, kinds = h->kinds;
         const uint64_t slotpack = h->slotpack;
-        if (s == 0) {
-            ucs[c].alpha = P.alpha32[c];
-            ucs[c].wz = h->wz;
-            ucs[c].nslot = __popc(mask);
+        int nb = 0, np = 0;
+        for (int pass = 0; pass < 2; ++pass) {
+            for (uint32_t m = mask; m; m &= m - 1u) {
+                const int k = __ffs(m) - 1;
+                const int s = (int)((slotpack >> (4 * k)) & 0xFu);
+                const int kind = (kinds >> (8 * s)) & 0xff;
+                const float* sp = h->sp[s];
+                if (pass == 0 && kind == MAP_BW)
+                    ucs[c].slot[nb++] = make_float4(sp[SP_M], sp[SP_G2], sp[SP_GINVA], __int_as_float(k));
+                else if (pass == 1 && kind == MAP_POW)
+                    ucs[c].slot[nb + np++] = make_float4(sp[SP_DEL], sp[SP_INVPOWN], 0.f, __int_as_float(k));
+            }
         }
-        for (uint32_t m = mask; m; m &= m - 1u) {
-            const int k = __ffs(m) - 1;
-            if ((int)((slotpack >> (4 * k)) & 0xFu) != s) continue;
-            const int kind = (h->kinds >> (8 * s)) & 0xff;
-            const float* sp = h->sp[s];
-            float4 r;
-            if (kind == MAP_BW) r = make_float4(sp[SP_M], sp[SP_G2], sp[SP_GINVA], 0.f);
-            else r = make_float4(sp[SP_DEL], sp[SP_INVPOWN], 0.f, 0.f);
-            r.w = __int_as_float(k | (kind << 8));
-            ucs[c].slot[s] = r;
-        }
+        ucs[c].alpha = P.alpha32[c];
+        ucs[c].wz = h->wz;
+        ucs[c].nbw = nb;
+        ucs[c].npw = np;
     }
     __syncthreads();
 
@@ -185,9 +193,10 @@ __global__ void __launch_bounds__(PASS_THREADS, MINB) k_union(Params P, PassArgs
 #pragma unroll
         for (int k = 0; k < DM; ++k)
             if (sh.has(k)) Pt[k] = C.p[0][k];
+        // cell entries now, the scan after part J (their latency hides behind it)
+        uint32_t ce[DM];
 #pragma unroll
-        for (int k = 0; k < DM; ++k)
-            if (sh.has(k)) Uw[k * 32 + lane] = (uint16_t)union_interval(P, k, C.p[0][k]);
+        for (int k = 0; k < DM; ++k) ce[k] = sh.has(k) ? union_cell_entry(P, k, C.p[0][k]) : 0u;
 
         // ---- J: α_c times the Jacobians of channel c's mapped coordinates ------
         const int own = MODE == 0 ? cseg : C.cq[0];
@@ -196,31 +205,36 @@ __global__ void __launch_bounds__(PASS_THREADS, MINB) k_union(Params P, PassArgs
 #pragma unroll 2
         for (int c2 = 0; c2 < K; ++c2) {
             const UnionChan& ch = ucs[c2];
-            const int ns = ch.nslot;
+            const int nb = ch.nbw, ne = ch.nbw + ch.npw;
             float J = 1.f, F = 1.f, as = 0.f;
-#pragma unroll
-            for (int s = 0; s < MAXMAP; ++s) {
-                if (s < ns) {
-                    const float4 r = ch.slot[s];
-                    const int kb = __float_as_int(r.w);
-                    const float pk = Pt[kb & 0xff];
-                    if ((kb >> 8) == MAP_BW) {
-                        const float dp = pk - r.x;
-                        const float jfac = Prec<float>::div(r.z, fmaf(dp, dp, r.y));
-                        J *= jfac;
-                        F *= jfac;
-                    } else if ((kb >> 8) == MAP_POW) {
-                        J *= 0.2f * Prec<float>::powm08(pk);  // 1/φ' = 1/(5 x^4) with x = p^(1/5)
-                        if (with_f) F *= Prec<float>::powm08(pk + r.x) * r.y;
-                    }
-                    const float u = pk - gc;
-                    as += u * u * k2;
-                }
+#pragma unroll 1
+            for (int s = 0; s < nb; ++s) {
+                const float4 r = ch.slot[s];
+                const float pk = Pt[__float_as_int(r.w)];
+                const float dp = pk - r.x;
+                const float jfac = Prec<float>::div(r.z, fmaf(dp, dp, r.y));
+                J *= jfac;
+                F *= jfac;
+                const float u = pk - gc;
+                as += u * u * k2;
+            }
+#pragma unroll 1
+            for (int s = nb; s < ne; ++s) {
+                const float4 r = ch.slot[s];
+                const float pk = Pt[__float_as_int(r.w)];
+                J *= 0.2f * Prec<float>::powm08(pk);  // 1/φ' = 1/(5 x^4) with x = p^(1/5)
+                if (with_f) F *= Prec<float>::powm08(pk + r.x) * r.y;
+                const float u = pk - gc;
+                as += u * u * k2;
             }
             const float a = ch.alpha;
             Jw[lane * UNION_JSTR + c2] = (a != 0.f && c2 != own) ? a * J : 0.f;
             if (with_f) f += ch.wz * Prec<float>::exp2_(as - Aq) * F;
         }
+        // ---- S (end): intervals from the cell entries --------------------------
+#pragma unroll
+        for (int k = 0; k < DM; ++k)
+            if (sh.has(k)) Uw[k * 32 + lane] = (uint16_t)union_interval(P, k, Pt[k], ce[k]);
         __syncwarp();
 
         // ---- U: densities of the warp's calls, channels 2l and 2l+1 in lane l --

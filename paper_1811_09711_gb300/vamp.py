@@ -85,7 +85,7 @@ class PassResult(C.Structure):
 
 class PipePeaks(C.Structure):
     _fields_ = [("fp32_lane_ops", C.c_double), ("fp64_lane_ops", C.c_double), ("xu_lane_ops", C.c_double),
-                ("lds_wavefronts", C.c_double)]
+                ("lds_wavefronts", C.c_double), ("l2_read_bytes", C.c_double)]
 
 
 class RequestResult(C.Structure):
@@ -364,8 +364,8 @@ class Vamp:
     def select_family(self, family: str) -> str:
         """Pin the pass kernel to the first candidate of a kernel family
         ("k_pass": the channel loop per call, whose FP32-eval arithmetic the
-        batch and server kernels share; "k_scan": lookups per coordinate);
-        returns its name."""
+        batch and server kernels share; "k_union": the pass over
+        per-coordinate interval tables); returns its name."""
         for i in range(self.kernel_candidates()):
             self.select_kernel(i)
             name = self.kernel_name(0)

@@ -98,6 +98,8 @@ def test_stratified_instances_in_a_batch_equal_alone(V, precision, tol):
              P.batch_instance(3), P.ring(3, 5).replace(stratified=1)]
     batch = V.Batch(probs, precision=precision, autotune=False)
     alone = [V.Vamp(pr, precision=precision) for pr in probs]
+    for g in alone:
+        g.select_family("k_pass")  # the FP32-eval arithmetic of the batch kernel
     for it, calls in enumerate((40_000, 40_000, 120_000)):
         rb = batch.iterate([calls] * len(probs), it, adapt=3)
         for i, g in enumerate(alone):
@@ -143,6 +145,7 @@ def test_stratified_requests_in_a_server_equal_alone(V, precision, tol):
     srv.close()
     for rid, (pr, iters, calls) in zip(ids, reqs):
         g = V.Vamp(pr, precision=precision)
+        g.select_family("k_pass")  # the FP32-eval arithmetic of the server's multi-instance kernel
         for it in range(iters):
             ra = g.sample_pass(calls, it)
             g.refine_grids()
