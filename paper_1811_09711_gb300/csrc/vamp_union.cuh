@@ -34,13 +34,17 @@ namespace vamp {
 constexpr int UNION_JSTR = UNION_SLOTS + 2;  // floats per call row of the channel factors (8-byte rows, 2-way banks)
 
 // A channel's terms for part J, copied into shared memory once per CTA:
-// α_c, the matching peak's weight, and its mapped coordinates, the nbw
+// α_c; the matching peak's weight times the product of its power-law
+// normalisations 1/powN; 0.2^npw; and its mapped coordinates, the nbw
 // Breit-Wigner ones first (m, Γ², Γ/A, k), then the npw power-law ones
-// (δ, 1/powN, 0, k), so that part J runs two loops of uniform trip count
-// with no test of the map kind.
+// (δ, 0, 0, k), so that part J runs two loops of uniform trip count with no
+// test of the map kind.  A channel's power-law factors enter as one
+// exponential of summed logarithms: Π 0.2 p^(-4/5) = 0.2^npw
+// 2^(-0.8 Σ log2 p) for the Jacobian and Π (p + δ)^(-4/5) joins the
+// Gaussian exponent of the peak.
 struct UnionChan {
-    float alpha, wz;
-    int nbw, npw;
+    float alpha, wz, jpw;
+    int nslot;            // nbw | npw << 8
     float4 slot[MAXMAP];  // {c0, c1, c2, bits of k}
 };
 static_assert(sizeof(UnionChan) == 80, "UnionChan layout");
@@ -70,6 +74,22 @@ __device__ __forceinline__ float2 ld_row(const float2* p)
     float2 v;
     asm("ld.global.nc.L1::no_allocate.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
     return v;
+}
+
+// This CTA's share of [base, base + bytes) prefetched into L2 with bulk
+// prefetches (16-byte granules; whole ranges are split evenly over the grid).
+__device__ __forceinline__ void l2_prefetch_share(const void* base, size_t bytes)
+{
+    const size_t g16 = bytes / 16;
+    const size_t per = (g16 + gridDim.x - 1) / gridDim.x;
+    const size_t b0 = (size_t)blockIdx.x * per;
+    if (b0 >= g16) return;
+    const size_t n16 = min(per, g16 - b0);
+    const char* p = static_cast<const char*>(base) + b0 * 16;
+    for (size_t o = 0; o < n16 * 16; o += 65536) {
+        const uint32_t len = (uint32_t)min((size_t)65536, n16 * 16 - o);
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p + o), "r"(len) : "memory");
+    }
 }
 
 // Cell entry of x on coordinate k (the first step of union_interval).
@@ -111,6 +131,14 @@ __global__ void __launch_bounds__(PASS_THREADS, MINB) k_union(Params P, PassArgs
     constexpr int B = PASS_THREADS;
 
     UnionChan* ucs = reinterpret_cast<UnionChan*>(smem + L.ch);
+    // the interval tables and lookup blocks into L2 at once (after a cold
+    // cache their first reads would each wait on a DRAM miss)
+    if (tid == 0) {
+        l2_prefetch_share(P.uD, (size_t)d * P.uMax * UNION_SLOTS * sizeof(float));
+        l2_prefetch_share(P.uC, (size_t)d * UNION_CELLS * sizeof(uint32_t));
+        l2_prefetch_share(P.uU, (size_t)d * P.uMax * sizeof(float));
+        l2_prefetch_share(P.lk32, (size_t)K * sh.bytes());
+    }
     // channel slots >= K keep factor 0 (their density rows are 0 as well)
     for (int i = tid; i < NW * 32 * UNION_JSTR; i += PASS_THREADS) Js[i] = 0.f;
     // part J's channel terms from the lookup-block headers (one thread per
@@ -120,22 +148,26 @@ __global__ void __launch_bounds__(PASS_THREADS, MINB) k_union(Params P, PassArgs
         const uint32_t mask = h->mask, kinds = h->kinds;
         const uint64_t slotpack = h->slotpack;
         int nb = 0, np = 0;
+        float wz = h->wz, jpw = 1.f;
         for (int pass = 0; pass < 2; ++pass) {
             for (uint32_t m = mask; m; m &= m - 1u) {
                 const int k = __ffs(m) - 1;
                 const int s = (int)((slotpack >> (4 * k)) & 0xFu);
                 const int kind = (kinds >> (8 * s)) & 0xff;
                 const float* sp = h->sp[s];
-                if (pass == 0 && kind == MAP_BW)
+                if (pass == 0 && kind == MAP_BW) {
                     ucs[c].slot[nb++] = make_float4(sp[SP_M], sp[SP_G2], sp[SP_GINVA], __int_as_float(k));
-                else if (pass == 1 && kind == MAP_POW)
-                    ucs[c].slot[nb + np++] = make_float4(sp[SP_DEL], sp[SP_INVPOWN], 0.f, __int_as_float(k));
+                } else if (pass == 1 && kind == MAP_POW) {
+                    ucs[c].slot[nb + np++] = make_float4(sp[SP_DEL], 0.f, 0.f, __int_as_float(k));
+                    wz *= sp[SP_INVPOWN];
+                    jpw *= 0.2f;
+                }
             }
         }
         ucs[c].alpha = P.alpha32[c];
-        ucs[c].wz = h->wz;
-        ucs[c].nbw = nb;
-        ucs[c].npw = np;
+        ucs[c].wz = wz;
+        ucs[c].jpw = jpw;
+        ucs[c].nslot = nb | (np << 8);
     }
     __syncthreads();
 
@@ -202,39 +234,48 @@ __global__ void __launch_bounds__(PASS_THREADS, MINB) k_union(Params P, PassArgs
         const int own = MODE == 0 ? cseg : C.cq[0];
         const float Aq = C.Aexp[0];
         float f = C.f[0];
-#pragma unroll 2
-        for (int c2 = 0; c2 < K; ++c2) {
-            const UnionChan& ch = ucs[c2];
-            const int nb = ch.nbw, ne = ch.nbw + ch.npw;
-            float J = 1.f, F = 1.f, as = 0.f;
+        // two halves of the channels; the interval scans (whose cell entries
+        // were loaded above) run between them, so that their reads of U_k
+        // overlap the second half
+        for (int half = 0; half < 2; ++half) {
+            const int c_lo = half == 0 ? 0 : K / 2, c_hi = half == 0 ? K / 2 : K;
+#pragma unroll 4
+            for (int c2 = c_lo; c2 < c_hi; ++c2) {
+                const UnionChan& ch = ucs[c2];
+                const int nb = ch.nslot & 0xff, ne = nb + (ch.nslot >> 8);
+                float J = 1.f, F = 1.f, as = 0.f, lp = 0.f, lq = 0.f;
 #pragma unroll 1
-            for (int s = 0; s < nb; ++s) {
-                const float4 r = ch.slot[s];
-                const float pk = Pt[__float_as_int(r.w)];
-                const float dp = pk - r.x;
-                const float jfac = Prec<float>::div(r.z, fmaf(dp, dp, r.y));
-                J *= jfac;
-                F *= jfac;
-                const float u = pk - gc;
-                as += u * u * k2;
-            }
+                for (int s = 0; s < nb; ++s) {
+                    const float4 r = ch.slot[s];
+                    const float pk = Pt[__float_as_int(r.w)];
+                    const float dp = pk - r.x;
+                    const float jfac = Prec<float>::div(r.z, fmaf(dp, dp, r.y));
+                    J *= jfac;
+                    F *= jfac;
+                    const float u = pk - gc;
+                    as += u * u * k2;
+                }
 #pragma unroll 1
-            for (int s = nb; s < ne; ++s) {
-                const float4 r = ch.slot[s];
-                const float pk = Pt[__float_as_int(r.w)];
-                J *= 0.2f * Prec<float>::powm08(pk);  // 1/φ' = 1/(5 x^4) with x = p^(1/5)
-                if (with_f) F *= Prec<float>::powm08(pk + r.x) * r.y;
-                const float u = pk - gc;
-                as += u * u * k2;
+                for (int s = nb; s < ne; ++s) {
+                    const float4 r = ch.slot[s];
+                    const float pk = Pt[__float_as_int(r.w)];
+                    lp += __log2f(pk);
+                    if (with_f) lq += __log2f(pk + r.x);
+                    const float u = pk - gc;
+                    as += u * u * k2;
+                }
+                if (ne > nb) J *= ch.jpw * Prec<float>::exp2_(-0.8f * lp);  // Π 1/φ' = Π 0.2 p^(-4/5)
+                const float a = ch.alpha;
+                Jw[lane * UNION_JSTR + c2] = (a != 0.f && c2 != own) ? a * J : 0.f;
+                if (with_f) f += ch.wz * Prec<float>::exp2_(fmaf(-0.8f, lq, as - Aq)) * F;
             }
-            const float a = ch.alpha;
-            Jw[lane * UNION_JSTR + c2] = (a != 0.f && c2 != own) ? a * J : 0.f;
-            if (with_f) f += ch.wz * Prec<float>::exp2_(as - Aq) * F;
-        }
-        // ---- S (end): intervals from the cell entries --------------------------
+            if (half == 0) {
+                // ---- S (end): intervals from the cell entries --------------------
 #pragma unroll
-        for (int k = 0; k < DM; ++k)
-            if (sh.has(k)) Uw[k * 32 + lane] = (uint16_t)union_interval(P, k, Pt[k], ce[k]);
+                for (int k = 0; k < DM; ++k)
+                    if (sh.has(k)) Uw[k * 32 + lane] = (uint16_t)union_interval(P, k, Pt[k], ce[k]);
+            }
+        }
         __syncwarp();
 
         // ---- U: densities of the warp's calls, channels 2l and 2l+1 in lane l --
