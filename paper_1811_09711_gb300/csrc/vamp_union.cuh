@@ -57,8 +57,8 @@ __host__ __device__ constexpr int union_pstride(int DM) { return DM | 1; }
 __host__ __device__ constexpr UnionSmem union_smem_layout(int DM, int d, int n, int mode)
 {
     const int nw = PASS_THREADS / 32;
-    const int ds = SMEM_HEAD;
-    const int js = ds + (mode == 0 ? round_up(d * n * 8, 16) : 0);
+    const int ds = SMEM_HEAD;  // no shared d-values: calls add theirs to global memory
+    const int js = ds;
     const int ps = js + nw * 32 * UNION_JSTR * 4;
     const int us = ps + round_up(PASS_THREADS * union_pstride(DM) * 4, 16);
     const int ch = us + round_up(nw * DM * 32 * 2, 16);
@@ -122,7 +122,6 @@ __global__ void __launch_bounds__(PASS_THREADS, MINB) k_union(Params P, PassArgs
     const SH sh(P.lay32, P.d, P.n);
     const int d = sh.d(), n = sh.n(), dn = d * n, K = P.K;
     const UnionSmem L = union_smem_layout(DM, d, n, MODE);
-    double* Ds = reinterpret_cast<double*>(smem + L.ds);
     float* Js = reinterpret_cast<float*>(smem + L.js);
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     float* Jw = Js + wid * 32 * UNION_JSTR;                                       // factors of this warp's calls
@@ -206,9 +205,6 @@ __global__ void __launch_bounds__(PASS_THREADS, MINB) k_union(Params P, PassArgs
                 cseg = find_channel(P.Pc, K, i0);
                 seg_end = min(r1, P.Pc[cseg + 1]);
                 sft = P.shift[cseg];
-                for (int q = tid; q < dn; q += PASS_THREADS) Ds[q] = 0.0;
-                s1 = s2 = 0.0;
-                __syncthreads();
             }
             base = i0;
             end = min(seg_end, i0 + B);
@@ -321,12 +317,31 @@ __global__ void __launch_bounds__(PASS_THREADS, MINB) k_union(Params P, PassArgs
 
         // ---- C: weights and accumulation ----------------------------------------
         if (MODE == 0) {
-            phase_c_int<float, 1>(sh, C, sft, Ds, s1, s2, wm, bad);
-            i0 = end;
-            if (i0 >= seg_end) {
-                flush_segment(P, H, cseg, dn, Ds, s1, s2);
+            // weight, shifted sums and d-values (Eq. 15): each call adds its
+            // w^2 to its d bins in global memory (FP64 reductions, no wait);
+            // the warp's shifted sums go out once per batch
+            if (C.valid[0]) {
+                double w = C.g[0] > 0.f ? (double)(C.f[0] / C.g[0]) : 0.0;
+                if (!isfinite(w)) { bad = true; w = 0.0; }
+                const double dv = w - sft;
+                s1 = dv;
+                s2 = dv * dv;
+                wm = fmax(wm, fabs(w));  // signed integrands: w_max bounds |w|
+                const double w2 = w * w;
+                double* Dc = P.D + (size_t)cseg * dn;
+#pragma unroll
+                for (int k = 0; k < DM; ++k)
+                    if (sh.has(k)) atomicAdd(&Dc[k * n + ((C.jp[0][k >> 2] >> (8 * (k & 3))) & 0xff)], w2);
+            } else {
                 s1 = s2 = 0.0;
             }
+            s1 = warp_sum(s1);
+            s2 = warp_sum(s2);
+            if (lane == 0) {
+                atomicAdd(&P.csum[2 * cseg], s1);
+                atomicAdd(&P.csum[2 * cseg + 1], s2);
+            }
+            i0 = end;
         } else {
             phase_c_gen<float, 1>(P, A, sh, C, chunk, base, H.wcnt, H.woff, &H.round_total, wm, bad);
             chunk += gridDim.x;
