@@ -156,10 +156,11 @@ KERNEL_SOURCES = {
 
 # kernels of one timed adaptation step: allocation, sampling pass, pass
 # result, result copy (asynchronous form), rebinning, channel weights; the
-# union pass adds the four kernels that rebuild its interval tables after
-# the rebinning (edge images, sort, cell index, density rows)
+# union pass adds the kernel that reads its tables into L2 before the pass
+# and the four that rebuild them after the rebinning (edge images, sort,
+# cell index, density rows)
 KERNELS_PER_STEP = 6
-UNION_BUILD_KERNELS = 4
+UNION_EXTRA_KERNELS = 5
 
 
 def kernel_family(kernel: str) -> str:
@@ -696,7 +697,7 @@ def run_gpu(args):
            "last_pass": {"integral": last.integral, "sigma": math.sqrt(max(last.variance, 0.0)),
                          "efficiency": last.efficiency, "combined": last.combined,
                          "combined_sigma": last.combined_sigma, "chi2_dof": last.chi2_dof},
-           "e2e": e2e, "gpu_launches": (KERNELS_PER_STEP + (UNION_BUILD_KERNELS if union else 0)) * args.steps,
+           "e2e": e2e, "gpu_launches": (KERNELS_PER_STEP + (UNION_EXTRA_KERNELS if union else 0)) * args.steps,
            "roofline": roof, "clocks": clk}
     if batch is not None:
         res["batch"] = batch

@@ -76,22 +76,6 @@ __device__ __forceinline__ float2 ld_row(const float2* p)
     return v;
 }
 
-// This CTA's share of [base, base + bytes) prefetched into L2 with bulk
-// prefetches (16-byte granules; whole ranges are split evenly over the grid).
-__device__ __forceinline__ void l2_prefetch_share(const void* base, size_t bytes)
-{
-    const size_t g16 = bytes / 16;
-    const size_t per = (g16 + gridDim.x - 1) / gridDim.x;
-    const size_t b0 = (size_t)blockIdx.x * per;
-    if (b0 >= g16) return;
-    const size_t n16 = min(per, g16 - b0);
-    const char* p = static_cast<const char*>(base) + b0 * 16;
-    for (size_t o = 0; o < n16 * 16; o += 65536) {
-        const uint32_t len = (uint32_t)min((size_t)65536, n16 * 16 - o);
-        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p + o), "r"(len) : "memory");
-    }
-}
-
 // Cell entry of x on coordinate k (the first step of union_interval).
 __device__ __forceinline__ uint32_t union_cell_entry(const Params& P, int k, float x)
 {
@@ -130,14 +114,6 @@ __global__ void __launch_bounds__(PASS_THREADS, MINB) k_union(Params P, PassArgs
     constexpr int B = PASS_THREADS;
 
     UnionChan* ucs = reinterpret_cast<UnionChan*>(smem + L.ch);
-    // the interval tables and lookup blocks into L2 at once (after a cold
-    // cache their first reads would each wait on a DRAM miss)
-    if (tid == 0) {
-        l2_prefetch_share(P.uD, (size_t)d * P.uMax * UNION_SLOTS * sizeof(float));
-        l2_prefetch_share(P.uC, (size_t)d * UNION_CELLS * sizeof(uint32_t));
-        l2_prefetch_share(P.uU, (size_t)d * P.uMax * sizeof(float));
-        l2_prefetch_share(P.lk32, (size_t)K * sh.bytes());
-    }
     // channel slots >= K keep factor 0 (their density rows are 0 as well)
     for (int i = tid; i < NW * 32 * UNION_JSTR; i += PASS_THREADS) Js[i] = 0.f;
     // part J's channel terms from the lookup-block headers (one thread per
@@ -352,11 +328,20 @@ __global__ void __launch_bounds__(PASS_THREADS, MINB) k_union(Params P, PassArgs
     block_max_to(H, wm, MODE == 0 ? &P.sc->wmax_bits : &P.sc->gen_bmax_bits);
 }
 
+// An integration pass first reads its interval tables and lookup blocks
+// from memory with coalesced loads (launch_union_warm): after a cold cache
+// the pass's random first reads of each row would otherwise wait on DRAM
+// one by one.
 template <int D_, int NB_, int MINB>
 cudaError_t union_launch_t(const Params& P, int mode, const PassArgs& A, int grid, size_t smem, cudaStream_t s)
 {
-    if (mode) k_union<1, D_, NB_, MINB><<<grid, PASS_THREADS, smem, s>>>(P, A);
-    else k_union<0, D_, NB_, MINB><<<grid, PASS_THREADS, smem, s>>>(P, A);
+    if (mode) {
+        k_union<1, D_, NB_, MINB><<<grid, PASS_THREADS, smem, s>>>(P, A);
+    } else {
+        const cudaError_t e = launch_union_warm(P, s);
+        if (e != cudaSuccess) return e;
+        k_union<0, D_, NB_, MINB><<<grid, PASS_THREADS, smem, s>>>(P, A);
+    }
     return cudaGetLastError();
 }
 
