@@ -34,18 +34,21 @@ namespace vamp {
 constexpr int UNION_JSTR = UNION_SLOTS + 2;  // floats per call row of the channel factors (8-byte rows, 2-way banks)
 
 // A channel's terms for part J, copied into shared memory once per CTA:
-// α_c; the matching peak's weight times the product of its power-law
-// normalisations 1/powN; 0.2^npw; and its mapped coordinates, the nbw
-// Breit-Wigner ones first (m, Γ², Γ/A, k), then the npw power-law ones
-// (δ, 0, 0, k), so that part J runs two loops of uniform trip count with no
-// test of the map kind.  A channel's power-law factors enter as one
-// exponential of summed logarithms: Π 0.2 p^(-4/5) = 0.2^npw
-// 2^(-0.8 Σ log2 p) for the Jacobian and Π (p + δ)^(-4/5) joins the
-// Gaussian exponent of the peak.
+// α_c 0.2^npw; the matching peak's weight times the product of its
+// power-law normalisations 1/powN; the product of its Breit-Wigner
+// numerators Γ/A; and its mapped coordinates, the nbw Breit-Wigner ones
+// first (m, Γ², -, k), then the npw power-law ones (δ, -, -, k), so that
+// part J runs two loops of uniform trip count with no test of the map kind.
+// A channel's factors are formed with one reciprocal and two exponentials:
+// its Breit-Wigner Jacobians Γ/(A((p-m)² + Γ²)) as the constant over the
+// product of the denominators (each at least Γ² >= 1e-8, so the product of
+// four stays a normal FP32 number), its power-law Jacobians
+// Π 0.2 p^(-4/5) = 0.2^npw 2^(-0.8 Σ log2 p), and the peak's power-law
+// factors Π (p + δ)^(-4/5) joined to its Gaussian exponent.
 struct UnionChan {
-    float alpha, wz, jpw;
+    float alpha, wz, jc;  // α_c 0.2^npw, the peak weight Π 1/powN, Π_BW Γ/A
     int nslot;            // nbw | npw << 8
-    float4 slot[MAXMAP];  // {c0, c1, c2, bits of k}
+    float4 slot[MAXMAP];  // {c0, c1, -, bits of k}
 };
 static_assert(sizeof(UnionChan) == 80, "UnionChan layout");
 
@@ -123,7 +126,7 @@ __global__ void __launch_bounds__(PASS_THREADS, MINB) k_union(Params P, PassArgs
         const uint32_t mask = h->mask, kinds = h->kinds;
         const uint64_t slotpack = h->slotpack;
         int nb = 0, np = 0;
-        float wz = h->wz, jpw = 1.f;
+        float wz = h->wz, jc = 1.f, a5 = 1.f;
         for (int pass = 0; pass < 2; ++pass) {
             for (uint32_t m = mask; m; m &= m - 1u) {
                 const int k = __ffs(m) - 1;
@@ -131,17 +134,18 @@ __global__ void __launch_bounds__(PASS_THREADS, MINB) k_union(Params P, PassArgs
                 const int kind = (kinds >> (8 * s)) & 0xff;
                 const float* sp = h->sp[s];
                 if (pass == 0 && kind == MAP_BW) {
-                    ucs[c].slot[nb++] = make_float4(sp[SP_M], sp[SP_G2], sp[SP_GINVA], __int_as_float(k));
+                    ucs[c].slot[nb++] = make_float4(sp[SP_M], sp[SP_G2], 0.f, __int_as_float(k));
+                    jc *= sp[SP_GINVA];
                 } else if (pass == 1 && kind == MAP_POW) {
                     ucs[c].slot[nb + np++] = make_float4(sp[SP_DEL], 0.f, 0.f, __int_as_float(k));
                     wz *= sp[SP_INVPOWN];
-                    jpw *= 0.2f;
+                    a5 *= 0.2f;
                 }
             }
         }
-        ucs[c].alpha = P.alpha32[c];
+        ucs[c].alpha = P.alpha32[c] * a5;
         ucs[c].wz = wz;
-        ucs[c].jpw = jpw;
+        ucs[c].jc = jc;
         ucs[c].nslot = nb | (np << 8);
     }
     __syncthreads();
@@ -215,15 +219,13 @@ __global__ void __launch_bounds__(PASS_THREADS, MINB) k_union(Params P, PassArgs
             for (int c2 = c_lo; c2 < c_hi; ++c2) {
                 const UnionChan& ch = ucs[c2];
                 const int nb = ch.nslot & 0xff, ne = nb + (ch.nslot >> 8);
-                float J = 1.f, F = 1.f, as = 0.f, lp = 0.f, lq = 0.f;
+                float den = 1.f, as = 0.f, lp = 0.f, lq = 0.f;
 #pragma unroll 1
                 for (int s = 0; s < nb; ++s) {
                     const float4 r = ch.slot[s];
                     const float pk = Pt[__float_as_int(r.w)];
                     const float dp = pk - r.x;
-                    const float jfac = Prec<float>::div(r.z, fmaf(dp, dp, r.y));
-                    J *= jfac;
-                    F *= jfac;
+                    den *= fmaf(dp, dp, r.y);
                     const float u = pk - gc;
                     as += u * u * k2;
                 }
@@ -236,10 +238,12 @@ __global__ void __launch_bounds__(PASS_THREADS, MINB) k_union(Params P, PassArgs
                     const float u = pk - gc;
                     as += u * u * k2;
                 }
-                if (ne > nb) J *= ch.jpw * Prec<float>::exp2_(-0.8f * lp);  // Π 1/φ' = Π 0.2 p^(-4/5)
+                const float bw = Prec<float>::div(1.f, den);  // Π_BW ((p-m)² + Γ²)^-1
+                const float jb = ch.jc * bw;  // Π_BW 1/φ'
+                const float J = jb * (ne > nb ? Prec<float>::exp2_(-0.8f * lp) : 1.f);
                 const float a = ch.alpha;
                 Jw[lane * UNION_JSTR + c2] = (a != 0.f && c2 != own) ? a * J : 0.f;
-                if (with_f) f += ch.wz * Prec<float>::exp2_(fmaf(-0.8f, lq, as - Aq)) * F;
+                if (with_f) f += ch.wz * Prec<float>::exp2_(fmaf(-0.8f, lq, as - Aq)) * jb;
             }
             if (half == 0) {
                 // ---- S (end): intervals from the cell entries --------------------
