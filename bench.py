@@ -156,11 +156,10 @@ KERNEL_SOURCES = {
 
 # kernels of one timed adaptation step: allocation, sampling pass, pass
 # result, result copy (asynchronous form), rebinning, channel weights; the
-# union pass adds the kernel that reads its tables into L2 before the pass
-# and the four that rebuild them after the rebinning (edge images, sort,
-# cell index, density rows)
+# union pass adds the four that rebuild its interval tables after the
+# rebinning (edge images, sort, cell index, density rows)
 KERNELS_PER_STEP = 6
-UNION_EXTRA_KERNELS = 5
+UNION_EXTRA_KERNELS = 4
 
 
 def kernel_family(kernel: str) -> str:

@@ -75,9 +75,6 @@ void bind_union(Params& P, unsigned char* base);   // sets P.u* (null: no tables
 // Rebuilds the tables from P's master grids and lookup blocks (enqueued on s).
 cudaError_t launch_union_build(const Params& P, cudaStream_t s);
 size_t union_pass_smem(const Params& P, const PassVariant& v, int mode);
-// Reads the tables and the FP32 lookup blocks once with coalesced loads, so
-// that a following union pass finds them in L2 (enqueued on s).
-cudaError_t launch_union_warm(const Params& P, cudaStream_t s);
 
 // Host-side data derived from a vamp_config (vamp_setup.cu).
 struct Setup {

@@ -169,28 +169,6 @@ __global__ void k_union_rows(Params P)
     }
 }
 
-// Coalesced 16-byte reads of the density rows, cell entries, interval
-// values and FP32 lookup blocks, which leave their lines in L2; the sum only
-// keeps the loads alive: it is written to a padding word of the device
-// scalars in the unlikely case that it is exactly -1.  (Every region starts
-// 256-byte aligned; a tail of fewer than 16 bytes is not read.)
-__global__ void k_union_warm(Params P)
-{
-    const size_t m = (size_t)P.K * (P.n + 1);
-    const float4* a[4] = {reinterpret_cast<const float4*>(P.uD), reinterpret_cast<const float4*>(P.uC),
-                          reinterpret_cast<const float4*>(P.uU), reinterpret_cast<const float4*>(P.lk32)};
-    const size_t n16[4] = {(size_t)P.d * m * UNION_SLOTS / 4, (size_t)P.d * UNION_CELLS / 4, (size_t)P.d * m / 4,
-                           (size_t)P.K * P.lay32.bytes / 16};
-    float acc = 0.f;
-    const size_t t0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x, nt = (size_t)gridDim.x * blockDim.x;
-    for (int r = 0; r < 4; ++r)
-        for (size_t i = t0; i < n16[r]; i += nt) {
-            const float4 v = __ldcg(a[r] + i);
-            acc += (v.x + v.y) + (v.z + v.w);
-        }
-    if (acc == -1.0f) P.sc->pad0 = __float_as_uint(acc);
-}
-
 int sort_width(int m)
 {
     int np = 2;
@@ -246,16 +224,6 @@ cudaError_t launch_union_build(const Params& P, cudaStream_t s)
     k_union_sort<<<d, SORT_THREADS, sort_smem, s>>>(P, np);
     k_union_cells<<<dim3(UNION_CELLS / 256, d), 256, 0, s>>>(P);
     k_union_rows<<<dim3((m + ROWS_PER_BLOCK - 1) / ROWS_PER_BLOCK, d), 256, rows_smem, s>>>(P);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_union_warm(const Params& P, cudaStream_t s)
-{
-    int dev = 0, sms = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return e;
-    k_union_warm<<<(unsigned)sms * 4, 256, 0, s>>>(P);
     return cudaGetLastError();
 }
 

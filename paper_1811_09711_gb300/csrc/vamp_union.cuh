@@ -267,9 +267,7 @@ __global__ void __launch_bounds__(PASS_THREADS, MINB) k_union(Params P, PassArgs
                 const uint16_t* uk = Uw + k * 32;
 #pragma unroll
                 for (int i = 0; i < 32; ++i) {
-                    const float2 v = ld_row(row + (size_t)uk[i] * (UNION_SLOTS / 2));
-                    acc[i].x *= v.x;
-                    acc[i].y *= v.y;
+                    acc[i] = __fmul2_rn(acc[i], ld_row(row + (size_t)uk[i] * (UNION_SLOTS / 2)));  // packed FP32x2
                 }
             }
             float v[32];
@@ -334,20 +332,11 @@ __global__ void __launch_bounds__(PASS_THREADS, MINB) k_union(Params P, PassArgs
     block_max_to(H, wm, MODE == 0 ? &P.sc->wmax_bits : &P.sc->gen_bmax_bits);
 }
 
-// An integration pass first reads its interval tables and lookup blocks
-// from memory with coalesced loads (launch_union_warm): after a cold cache
-// the pass's random first reads of each row would otherwise wait on DRAM
-// one by one.
 template <int D_, int NB_, int MINB>
 cudaError_t union_launch_t(const Params& P, int mode, const PassArgs& A, int grid, size_t smem, cudaStream_t s)
 {
-    if (mode) {
-        k_union<1, D_, NB_, MINB><<<grid, PASS_THREADS, smem, s>>>(P, A);
-    } else {
-        const cudaError_t e = launch_union_warm(P, s);
-        if (e != cudaSuccess) return e;
-        k_union<0, D_, NB_, MINB><<<grid, PASS_THREADS, smem, s>>>(P, A);
-    }
+    if (mode) k_union<1, D_, NB_, MINB><<<grid, PASS_THREADS, smem, s>>>(P, A);
+    else k_union<0, D_, NB_, MINB><<<grid, PASS_THREADS, smem, s>>>(P, A);
     return cudaGetLastError();
 }
 
