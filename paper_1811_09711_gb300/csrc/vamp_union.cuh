@@ -94,8 +94,10 @@ __device__ __forceinline__ int union_interval(const Params& P, int k, float x, u
 {
     const int base = (int)(e & 0xffffu), span = (int)(e >> 16);
     const float* Uk = P.uU + (size_t)k * P.uMax + base;
-    int t = 0;
-    while (t < span && __ldg(Uk + t) <= x) ++t;
+    // most cells hold at most one value of U_k: one comparison, no loop
+    int t = (span > 0 && __ldg(Uk) <= x) ? 1 : 0;
+    if (t == 1 && span > 1)
+        while (t < span && __ldg(Uk + t) <= x) ++t;
     return max(base + t - 1, 0);
 }
 
