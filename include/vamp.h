@@ -315,16 +315,25 @@ vamp_status vamp_pass_kernel_name(const vamp_ctx *ctx, int32_t mode, char *buf, 
 
 /* Number of compiled pass-kernel variants that can run this context's shape
  * and sampling mode: the autotuner's candidates, in a fixed order
- * (shape-specialised kernels first, then the generic ones). */
+ * (shape-specialised staged-tile kernels "k_pass" first, then the generic
+ * one; for FP32-eval importance sampling with K <= 64 and K (n+1) <= 16384,
+ * then the union kernels "k_union", which find every channel's bin of p_k
+ * with one search in per-coordinate tables of all channels' edge images,
+ * Eq. 30 evaluated the same way). */
 vamp_status vamp_pass_kernel_candidates(const vamp_ctx *ctx, int32_t *count);
 
 /* Pins the context's pass kernels (integration and generation) to candidate
  * `index` (0 <= index < count of vamp_pass_kernel_candidates) instead of the
  * autotuner's pick at the first pass -- for tests that must run a given
  * variant and for reproducible timing.  Every candidate computes the same
- * pass; sums may differ in the order of floating-point additions.  The
- * choice holds until the context is destroyed.  INVALID_ARG for a bad index;
- * CUDA if the kernel's shared memory cannot be configured. */
+ * pass; sums may differ in the order of floating-point additions (and, in
+ * the FP32-eval form, in FP32 rounding).  The choice holds until the
+ * context is destroyed.  While a union kernel is in use (picked here or by
+ * the autotuner) the context also holds its interval tables on the device,
+ * about d K (n+1) 264 + d 2^18 bytes (27.6 MB for d = 14, K = 64, n = 100),
+ * rebuilt by every rebinning and state upload; choosing a staged-tile
+ * kernel frees them.  INVALID_ARG for a bad index; OOM if the tables cannot
+ * be allocated; CUDA if the kernel's shared memory cannot be configured. */
 vamp_status vamp_select_pass_kernel(vamp_ctx *ctx, int32_t index);
 
 /* ---- many independent integrations in one launch --------------------------
