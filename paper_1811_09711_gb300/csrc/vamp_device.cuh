@@ -16,7 +16,10 @@
 // the most bins any cell overlaps), so a lookup starts next to its answer.
 // Density entry n repeats entry n-1, so that a probe of edge ξ_n = 1 by a
 // point at (or rounded past) 1 needs no bounds check: it lands on entry n
-// with the last bin's density.
+// with the last bin's density.  In the FP64 blocks the rows of mapped
+// coordinates hold the images φ_c(ξ_j) of the edges (and their cell table
+// is over p): the maps are increasing, so the bin of φ_c^{-1}(p) is the bin
+// whose image holds p, found with no inverse map.
 #pragma once
 
 #include <cstddef>
@@ -445,7 +448,11 @@ __device__ __forceinline__ void forward_call(const Params& P, const SH& sh, int 
                 fr = Prec<T>::frac(t & ((1ull << 33) - 1ull));
             }
             const unsigned char* row = sh.row(blk, k);
-            const T* e = reinterpret_cast<const T*>(row);
+            // the grid's edges: the FP32 block row, or the FP64 master grid
+            // (whose values the FP64 block holds only for unmapped rows)
+            const T* e = sizeof(T) == 8
+                             ? reinterpret_cast<const T*>(P.edges64 + ((size_t)c * d + k) * (size_t)(n + 1))
+                             : reinterpret_cast<const T*>(row);
             x[k] = Prec<T>::lerp(__ldg(e + j), __ldg(e + j + 1), fr);
             jf[k] = j;
             g *= __ldg(reinterpret_cast<const T*>(row + sh.dens_off()) + j);
@@ -530,7 +537,9 @@ __device__ __forceinline__ void channel_rows(const Params& P, const SH& sh, cons
                         const T jfac = Prec<T>::div(GinvA, dp * dp + G2);
                         J[q] *= jfac;
                         F[q] *= jfac;
-                        xk[q] = (Prec<T>::atan_(dp * invG) + t0) * invA;
+                        // FP64 rows of mapped coordinates hold the images of
+                        // the edges: the lookup compares p itself
+                        if constexpr (sizeof(T) == 4) xk[q] = (Prec<T>::atan_(dp * invG) + t0) * invA;
                         const T u = p[q][k] - gc;
                         as[q] += u * u * k2;
                     }
@@ -542,8 +551,7 @@ __device__ __forceinline__ void channel_rows(const Params& P, const SH& sh, cons
                             // x = p^0.2 = p y^4 and 1/φ' = 1/(5 x^4) = y^4 / 5 from
                             // y = p^(-1/5): no division, no pow
                             const T y = Prec<T>::rinv5(p[q][k]), y2 = y * y, y4 = y2 * y2;
-                            J[q] *= T(0.2) * y4;
-                            xk[q] = p[q][k] * y4;
+                            J[q] *= T(0.2) * y4;  // the lookup compares p with the edge images
                         } else {
                             const T xx = Prec<T>::pow02(p[q][k]);
                             const T x2 = xx * xx;

@@ -218,8 +218,31 @@ __device__ __forceinline__ void derive_row_t(const Params& P, const BlkLayout& L
     T* e = reinterpret_cast<T*>(r);
     T* dnr = reinterpret_cast<T*>(r + L.Es * sizeof(T));
     unsigned char* tb = r + (L.Es + L.Dn) * sizeof(T);
+    // FP64 rows of mapped coordinates hold the images φ_c(ξ_j) of the edges
+    // (clamped at 0, the forward map's formula): a bin of x = φ_c^{-1}(p) is
+    // the bin whose image holds p, so the FP64 lookups compare p itself and
+    // need no inverse map; the forward map reads the edges from the master
+    // grid
+    int kind = MAP_ID;
+    const double* sp = nullptr;
+    if (sizeof(T) == 8) {
+        const ChanHdr<double>* h = reinterpret_cast<const ChanHdr<double>*>(lk + (size_t)c * L.bytes);
+        if ((h->mask >> k) & 1u) {
+            const int s = (int)((h->slotpack >> (4 * k)) & 0xFu);
+            kind = (h->kinds >> (8 * s)) & 0xff;
+            sp = h->sp[s];
+        }
+    }
     for (int j = lane; j <= n; j += nl) {
-        e[j] = (T)e64[j];
+        double v = e64[j];
+        if (kind == MAP_BW) {
+            v = sp[SP_M] + sp[SP_G] * Prec<double>::tan_(sp[SP_A] * v - sp[SP_T0]);
+        } else if (kind == MAP_POW) {
+            const double v2 = v * v, v4 = v2 * v2;
+            v = v4 * v;
+            if (v < Prec<double>::tiny()) v = Prec<double>::tiny();
+        }
+        e[j] = (T)(v > 0.0 ? v : 0.0);
         const int jb = j < n ? j : n - 1;  // entry n repeats bin n-1
         dnr[j] = (T)(1.0 / ((double)n * (e64[jb + 1] - e64[jb])));
     }

@@ -304,7 +304,7 @@ __global__ void __launch_bounds__(PASS_THREADS, MINB) k_pass(Params P, PassArgs 
     const size_t tile_bytes = (size_t)A.tile * S;
     double* Ds = reinterpret_cast<double*>(buf0 + 2 * tile_bytes);
     const int d = sh.d(), n = sh.n(), dn = d * n, K = P.K;
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int tid = threadIdx.x;
     constexpr int B = PASS_THREADS * CPT;
     const unsigned char* lk = Prec<T>::lk(P);
 
