@@ -518,6 +518,14 @@ __device__ __forceinline__ void channel_rows(const Params& P, const SH& sh, cons
     const uint32_t mask = h.mask, kinds = h.kinds, slow = h.slow;
     const uint64_t slotpack = h.slotpack;
     const T gc = Prec<T>::gcen(P), k2 = Prec<T>::gk2(P);
+    // FP64: the Breit-Wigner Jacobians Γ/(A((p-m)² + Γ²)) of the channel as
+    // one quotient of the products of numerators and denominators (one FP64
+    // division per channel instead of one per mapped coordinate; each
+    // denominator is at least Γ², so the product of four stays normal)
+    T bw_num = T(1), bw_den[CPT];
+    bool any_bw = false;
+#pragma unroll
+    for (int q = 0; q < CPT; ++q) bw_den[q] = T(1);
 #pragma unroll
     for (int k = 0; k < SH::DM; ++k) {
         if (sh.has(k)) {
@@ -534,14 +542,22 @@ __device__ __forceinline__ void channel_rows(const Params& P, const SH& sh, cons
 #pragma unroll
                     for (int q = 0; q < CPT; ++q) {
                         const T dp = p[q][k] - mass;
-                        const T jfac = Prec<T>::div(GinvA, dp * dp + G2);
-                        J[q] *= jfac;
-                        F[q] *= jfac;
-                        // FP64 rows of mapped coordinates hold the images of
-                        // the edges: the lookup compares p itself
-                        if constexpr (sizeof(T) == 4) xk[q] = (Prec<T>::atan_(dp * invG) + t0) * invA;
+                        if constexpr (sizeof(T) == 8) {
+                            // FP64 rows of mapped coordinates hold the images of
+                            // the edges: the lookup compares p itself
+                            bw_den[q] *= dp * dp + G2;
+                        } else {
+                            const T jfac = Prec<T>::div(GinvA, dp * dp + G2);
+                            J[q] *= jfac;
+                            F[q] *= jfac;
+                            xk[q] = (Prec<T>::atan_(dp * invG) + t0) * invA;
+                        }
                         const T u = p[q][k] - gc;
                         as[q] += u * u * k2;
+                    }
+                    if constexpr (sizeof(T) == 8) {
+                        bw_num *= GinvA;
+                        any_bw = true;
                     }
                 } else if (kind == MAP_POW) {
                     const T del = sp[SP_DEL], ipn = sp[SP_INVPOWN];
@@ -590,6 +606,16 @@ __device__ __forceinline__ void channel_rows(const Params& P, const SH& sh, cons
                     if (REC && q == 0) bins[k] = min(j, sh.n() - 1);
                     gp[q] *= dn[j];
                 }
+            }
+        }
+    }
+    if constexpr (sizeof(T) == 8) {
+        if (any_bw) {
+#pragma unroll
+            for (int q = 0; q < CPT; ++q) {
+                const T jb = Prec<T>::div(bw_num, bw_den[q]);
+                J[q] *= jb;
+                F[q] *= jb;
             }
         }
     }
