@@ -29,6 +29,7 @@
 namespace vamp {
 
 constexpr int DMAX = 16;      // largest supported dimension
+constexpr int PASS_THREADS_DEV = 256;  // threads per pass CTA (PASS_THREADS of vamp_internal.h)
 constexpr int MAXMAP = 4;     // mapped coordinates per channel / peak
 constexpr int MAX_BINS = 256; // largest supported bins per axis (table entries are bytes)
 
@@ -508,10 +509,13 @@ __device__ __forceinline__ void forward_call(const Params& P, const SH& sh, int 
 // bins, so one edge probe settles each bin and the unrolled row loop has no
 // branch other than the mapped-coordinate test; otherwise rows are tested
 // one by one and only the spanning ones search.
+// pw (FP64 pass kernel, else null): this thread's 0.2 p_k^(-4/5) per call q
+// and coordinate k at pw[(q DM + k) PASS_THREADS], computed once per call,
+// the power-law Jacobian of every channel that maps k.
 template <typename T, int CPT, bool REC, bool FAST, class SH>
 __device__ __forceinline__ void channel_rows(const Params& P, const SH& sh, const unsigned char* blk, bool with_f,
                                              const T (&p)[CPT][SH::DM], T (&J)[CPT], T (&F)[CPT], T (&gp)[CPT],
-                                             T (&as)[CPT], int* bins)
+                                             T (&as)[CPT], int* bins, const T* pw)
 {
     const int d = sh.d();
     const ChanHdr<T>& h = *reinterpret_cast<const ChanHdr<T>*>(blk);
@@ -564,10 +568,15 @@ __device__ __forceinline__ void channel_rows(const Params& P, const SH& sh, cons
 #pragma unroll
                     for (int q = 0; q < CPT; ++q) {
                         if constexpr (sizeof(T) == 8) {
-                            // x = p^0.2 = p y^4 and 1/φ' = 1/(5 x^4) = y^4 / 5 from
-                            // y = p^(-1/5): no division, no pow
-                            const T y = Prec<T>::rinv5(p[q][k]), y2 = y * y, y4 = y2 * y2;
-                            J[q] *= T(0.2) * y4;  // the lookup compares p with the edge images
+                            // 1/φ' = 1/(5 x^4) = y^4 / 5 with x = p^0.2 and
+                            // y = p^(-1/5): no division, no pow (the lookup
+                            // compares p with the edge images)
+                            if (pw) {
+                                J[q] *= pw[(q * SH::DM + k) * PASS_THREADS_DEV];
+                            } else {
+                                const T y = Prec<T>::rinv5(p[q][k]), y2 = y * y, y4 = y2 * y2;
+                                J[q] *= T(0.2) * y4;
+                            }
                         } else {
                             const T xx = Prec<T>::pow02(p[q][k]);
                             const T x2 = xx * xx;
@@ -625,14 +634,14 @@ template <typename T, int CPT, bool REC, class SH>
 __device__ __forceinline__ void channel_body(const Params& P, const SH& sh, const unsigned char* blk, T alpha_c,
                                              bool lookups, bool with_f, const T (&p)[CPT][SH::DM],
                                              const T (&A)[CPT], const bool (&skip)[CPT], T (&g)[CPT],
-                                             T (&f)[CPT], int* bins)
+                                             T (&f)[CPT], int* bins, const T* pw = nullptr)
 {
     const ChanHdr<T>& h = *reinterpret_cast<const ChanHdr<T>*>(blk);
     T J[CPT], F[CPT], gp[CPT], as[CPT];
 #pragma unroll
     for (int q = 0; q < CPT; ++q) { J[q] = T(1); F[q] = T(1); gp[q] = T(1); as[q] = T(0); }
-    if (h.slow == 0u) channel_rows<T, CPT, REC, true>(P, sh, blk, with_f, p, J, F, gp, as, bins);
-    else channel_rows<T, CPT, REC, false>(P, sh, blk, with_f, p, J, F, gp, as, bins);
+    if (h.slow == 0u) channel_rows<T, CPT, REC, true>(P, sh, blk, with_f, p, J, F, gp, as, bins, pw);
+    else channel_rows<T, CPT, REC, false>(P, sh, blk, with_f, p, J, F, gp, as, bins, pw);
     const T wz = h.wz;
 #pragma unroll
     for (int q = 0; q < CPT; ++q) {

@@ -15,7 +15,7 @@ namespace vamp {
 struct Params;
 template <typename T> struct MapRec;
 
-constexpr int PASS_THREADS = 256;  // threads per pass CTA
+constexpr int PASS_THREADS = 256;  // threads per pass CTA (PASS_THREADS_DEV in the device code)
 constexpr int SMEM_HEAD = 512;     // bytes of barriers and scratch before the tile buffers
 constexpr int REFINE_WARPS = 4;    // grid rows per refine CTA
 constexpr size_t TILE_BUDGET = 112 * 1024;  // pass-kernel shared memory per CTA (two CTAs per SM)

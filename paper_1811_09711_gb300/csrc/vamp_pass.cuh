@@ -35,6 +35,8 @@ __device__ __forceinline__ double warp_max(double v)
     return v;
 }
 
+static_assert(PASS_THREADS == PASS_THREADS_DEV, "device copy of the CTA size");
+
 struct SmemHead {
     uint64_t bar[2];
     int abort;
@@ -130,7 +132,7 @@ __device__ __forceinline__ void phase_a(const Params& P, const SH& sh, uint32_t 
 // Phase B for one staged tile: channels t*tile .. of the tile buffer tb.
 template <typename T, int MODE, int CPT, class SH>
 __device__ __forceinline__ void tile_compute(const Params& P, const SH& sh, const unsigned char* tb, int t, int tile,
-                                             int cseg, Calls<T, CPT, SH::DM>& C)
+                                             int cseg, Calls<T, CPT, SH::DM>& C, const T* pw = nullptr)
 {
     const int S = sh.bytes();
     const int cnt = min(tile, P.K - t * tile);
@@ -142,7 +144,7 @@ __device__ __forceinline__ void tile_compute(const Params& P, const SH& sh, cons
 #pragma unroll
         for (int q = 0; q < CPT; ++q) skip[q] = (MODE == 1) && (C.cq[q] == c2);
         channel_body<T, CPT, false>(P, sh, tb + (size_t)cl * S, a, lookups, P.matching != 0, C.p, C.Aexp, skip,
-                                    C.g, C.f, nullptr);
+                                    C.g, C.f, nullptr, pw);
     }
 }
 
@@ -307,6 +309,20 @@ __global__ void __launch_bounds__(PASS_THREADS, MINB) k_pass(Params P, PassArgs 
     const int tid = threadIdx.x;
     constexpr int B = PASS_THREADS * CPT;
     const unsigned char* lk = Prec<T>::lk(P);
+    // FP64: the power-law Jacobian 0.2 p_k^(-4/5) of each coordinate of this
+    // thread's call, computed once per call instead of once per channel that
+    // maps k (after the tiles and the d-values; DMAX x PASS_THREADS doubles
+    // are reserved by smem_for_budget)
+    constexpr bool kPW = sizeof(T) == 8 && CPT == 1;
+    T* pwS = nullptr;
+    if constexpr (kPW) {
+        // used only where the launch reserved the space (see smem_for_budget)
+        unsigned dsm = 0;
+        asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dsm));
+        const size_t off = SMEM_HEAD + 2 * tile_bytes + (MODE == 0 ? (size_t)dn * 8 : 0);
+        if ((size_t)dsm >= off + (size_t)DM * PASS_THREADS * sizeof(T))
+            pwS = reinterpret_cast<T*>(smem + off);
+    }
 
     // ---- work of this CTA ---------------------------------------------------
     int64_t r0 = 0, r1 = 0;
@@ -383,6 +399,17 @@ __global__ void __launch_bounds__(PASS_THREADS, MINB) k_pass(Params P, PassArgs 
         // ---- phase A: own channel forward map, integrand --------------------
         Calls<T, CPT, DM> C;
         phase_a<T, MODE, CPT>(P, sh, A.field, base, end, cseg, C);
+        if constexpr (kPW) {
+            if (pwS) {
+#pragma unroll
+                for (int k = 0; k < DM; ++k) {
+                    if (sh.has(k)) {
+                        const T y = Prec<T>::rinv5(C.p[0][k]), y2 = y * y;
+                        pwS[k * PASS_THREADS + tid] = T(0.2) * (y2 * y2);
+                    }
+                }
+            }
+        }
 
         // ---- phase B: every channel's term of g(p) (and the matching peaks) --
         for (int t = 0; t < ntiles; ++t) {
@@ -395,7 +422,8 @@ __global__ void __launch_bounds__(PASS_THREADS, MINB) k_pass(Params P, PassArgs 
                     H.abort = 1;
                 }
             }
-            if (!H.abort) tile_compute<T, MODE, CPT>(P, sh, buf0 + b * tile_bytes, t, A.tile, cseg, C);
+            if (!H.abort)
+                tile_compute<T, MODE, CPT>(P, sh, buf0 + b * tile_bytes, t, A.tile, cseg, C, pwS ? pwS + tid : nullptr);
             __syncthreads();
             if (H.abort) goto drain;
             if (streaming && tid == 0 && issued < total_uses) {

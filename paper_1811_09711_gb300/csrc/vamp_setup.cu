@@ -304,12 +304,22 @@ void smem_for_budget(const Params& P, int fp32, size_t budget, int* tile, size_t
 {
     const size_t S = (size_t)(fp32 ? P.lay32.bytes : P.lay64.bytes);
     const size_t ds = (size_t)P.d * P.n * 8;
-    long t = budget > SMEM_HEAD + ds ? (long)((budget - SMEM_HEAD - ds) / (2 * S)) : 1;
+    // FP64: each thread's power-law Jacobians of its call, one per coordinate,
+    // where they fit beside one tile in a block's largest shared memory (the
+    // kernel computes them per channel otherwise)
+    size_t pw = fp32 ? 0 : (size_t)DMAX * PASS_THREADS * 8;
+    int dev = 0, maxsm = 0;
+    if (pw && cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess &&
+        SMEM_HEAD + 2 * S + ds + pw > (size_t)maxsm)
+        pw = 0;
+    const size_t fixed = SMEM_HEAD + ds + pw;
+    long t = budget > fixed ? (long)((budget - fixed) / (2 * S)) : 1;
     if (t < 1) t = 1;
     if (t > P.K) t = P.K;
     *tile = (int)t;
-    *smem_int = SMEM_HEAD + 2 * (size_t)t * S + ds;
-    *smem_gen = SMEM_HEAD + 2 * (size_t)t * S;
+    *smem_int = SMEM_HEAD + 2 * (size_t)t * S + ds + pw;
+    *smem_gen = SMEM_HEAD + 2 * (size_t)t * S + pw;
 }
 }  // namespace
 
