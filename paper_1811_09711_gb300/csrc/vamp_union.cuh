@@ -231,7 +231,7 @@ __global__ void __launch_bounds__(PASS_THREADS, MINB) k_union(Params P, PassArgs
                     const float dp = pk - r.x;
                     den *= fmaf(dp, dp, r.y);
                     const float u = pk - gc;
-                    as += u * u * k2;
+                    as = fmaf(u, u, as);  // Σ (p_k - c)², times k2 once per channel
                 }
 #pragma unroll 1
                 for (int s = nb; s < ne; ++s) {
@@ -240,14 +240,14 @@ __global__ void __launch_bounds__(PASS_THREADS, MINB) k_union(Params P, PassArgs
                     lp += __log2f(pk);
                     if (with_f) lq += __log2f(pk + r.x);
                     const float u = pk - gc;
-                    as += u * u * k2;
+                    as = fmaf(u, u, as);  // Σ (p_k - c)², times k2 once per channel
                 }
                 const float bw = Prec<float>::div(1.f, den);  // Π_BW ((p-m)² + Γ²)^-1
                 const float jb = ch.jc * bw;  // Π_BW 1/φ'
                 const float J = jb * (ne > nb ? Prec<float>::exp2_(-0.8f * lp) : 1.f);
                 const float a = ch.alpha;
                 Jw[lane * UNION_JSTR + c2] = (a != 0.f && c2 != own) ? a * J : 0.f;
-                if (with_f) f += ch.wz * Prec<float>::exp2_(fmaf(-0.8f, lq, as - Aq)) * jb;
+                if (with_f) f += ch.wz * Prec<float>::exp2_(fmaf(-0.8f, lq, fmaf(as, k2, -Aq))) * jb;
             }
             if (half == 0) {
                 // ---- S (end): intervals from the cell entries --------------------
