@@ -16,15 +16,20 @@
 //
 // Per batch of PASS_THREADS calls (one per thread), as k_pass where not said:
 //   A  Philox words, channel, forward map, own term, integrand;
-//   S  interval u_k of p_k on every coordinate (cell entry, short scan);
+//   S  cell entries of p_k on every coordinate (their scans run between the
+//      two halves of part J, so that the reads of U_k overlap it);
 //   J  per channel c: α_c × the Jacobians of its mapped coordinates at p
 //      (0 for the own and for switched-off channels) into shared memory, and
-//      the matching integrand peak;
+//      the matching integrand peak -- one reciprocal and at most two
+//      exponentials per channel;
 //   U  per warp, its 32 calls transposed: lane l multiplies the densities of
-//      channels 2l, 2l+1 on every coordinate (one float2 of the call's row)
-//      into the factors of J; a reduce-scatter over the lanes leaves
-//      Σ_c α_c g_c/φ'_c of call i in lane i;
-//   C  weights, sums, d-values (integration) or acceptance (generation).
+//      channels 2l, 2l+1 on every coordinate (one float2 of the call's row,
+//      through L1, packed FP32x2 products) into the factors of J; a
+//      reduce-scatter over the lanes leaves Σ_c α_c g_c/φ'_c of call i in
+//      lane i;
+//   C  weights; integration: shifted sums per warp and each call's w^2 added
+//      to its d bins in global memory (FP64 reductions, no CTA barrier in
+//      the batch loop); generation: acceptance and ordered compaction.
 #pragma once
 
 #include "vamp_pass.cuh"
