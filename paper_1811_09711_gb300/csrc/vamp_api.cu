@@ -155,17 +155,26 @@ VariantShape shape_of(const vamp_ctx* c, const PassVariant* v)
     return s;
 }
 
-// Allocates the union pass's interval tables (once) and enqueues their
-// build from the current grids; from then on every grid change rebuilds them.
+// Allocates the union pass's interval tables once; false (and the
+// allocation error cleared) where the device has no room for them.
+bool union_alloc(vamp_ctx* c)
+{
+    if (c->uni_buf) return true;
+    void* b = nullptr;
+    if (cudaMalloc(&b, vamp::union_bytes(c->d, c->K, c->n)) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    c->uni_buf = b;
+    vamp::bind_union(c->prm, (unsigned char*)b);
+    return true;
+}
+
+// Allocates the interval tables and enqueues their build from the current
+// grids; from then on every grid change rebuilds them.
 vamp_status union_enable(vamp_ctx* c)
 {
-    if (!c->uni_buf) {
-        void* b = nullptr;
-        if (cudaMalloc(&b, vamp::union_bytes(c->d, c->K, c->n)) != cudaSuccess)
-            return fail(c, VAMP_ERR_OOM, "interval tables of the union pass");
-        c->uni_buf = b;
-        vamp::bind_union(c->prm, (unsigned char*)b);
-    }
+    if (!union_alloc(c)) return fail(c, VAMP_ERR_OOM, "interval tables of the union pass");
     VAMP_CK(c, vamp::launch_union_build(c->prm, c->stream));
     c->uni_on = 1;
     return VAMP_OK;
@@ -193,7 +202,7 @@ vamp_status use_variant(vamp_ctx* c, const PassVariant* v)
     if (v->uni && !c->uni_on) {
         const vamp_status us = union_enable(c);
         if (us != VAMP_OK) return us;
-    } else if (!v->uni && c->uni_on) {
+    } else if (!v->uni && c->uni_buf) {
         union_disable(c);
     }
     const VariantShape s = shape_of(c, v);
@@ -213,7 +222,14 @@ vamp_status use_variant(vamp_ctx* c, const PassVariant* v)
 
 vamp_status choose_variant(vamp_ctx* c, int64_t n_calls)
 {
-    const std::vector<const PassVariant*> cand = candidates_of(c);
+    std::vector<const PassVariant*> cand = candidates_of(c);
+    // the union kernels run on their interval tables: where the device has
+    // no room for those, the staged-tile kernels are chosen among alone
+    const bool any_uni = std::any_of(cand.begin(), cand.end(), [](const PassVariant* v) { return v->uni != 0; });
+    const bool reduced = any_uni && !union_alloc(c);
+    if (reduced)
+        cand.erase(std::remove_if(cand.begin(), cand.end(), [](const PassVariant* v) { return v->uni != 0; }),
+                   cand.end());
     if (cand.empty()) return fail(c, VAMP_ERR_INVALID_ARG, "no pass kernel for this shape");
     for (const PassVariant* v : cand) {
         const VariantShape s = shape_of(c, v);
@@ -280,7 +296,7 @@ vamp_status choose_variant(vamp_ctx* c, int64_t n_calls)
         VAMP_CK(c, cudaMemsetAsync(c->prm.sc, 0, HEAD_BYTES, c->stream));
         VAMP_CK(c, cudaStreamSynchronize(c->stream));
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tuned[key] = best;
+        if (!reduced) g_tuned[key] = best;  // a choice made without the union kernels is not kept
     }
     return use_variant(c, best);
 }
