@@ -333,7 +333,10 @@ vamp_status vamp_pass_kernel_candidates(const vamp_ctx *ctx, int32_t *count);
  * about d K (n+1) 264 + d 2^18 bytes (27.6 MB for d = 14, K = 64, n = 100),
  * rebuilt by every rebinning and state upload; choosing a staged-tile
  * kernel frees them.  INVALID_ARG for a bad index; OOM if the tables cannot
- * be allocated; CUDA if the kernel's shared memory cannot be configured. */
+ * be allocated; CUDA if the kernel's shared memory cannot be configured.
+ * (The autotuner itself, where the device has no room for the tables,
+ * chooses among the staged-tile kernels alone and does not remember that
+ * choice for later contexts.) */
 vamp_status vamp_select_pass_kernel(vamp_ctx *ctx, int32_t index);
 
 /* ---- many independent integrations in one launch --------------------------
