@@ -249,7 +249,9 @@ template <> struct Prec<double> {
         const int r = ne - 5 * a;
         const double w = __longlong_as_double((b & 0x000FFFFFFFFFFFFFll) | ((long long)(1023 - r) << 52));
         float s;
-        asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(s) : "f"(-0.2f * __log2f((float)w)));
+        float l;
+        asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l) : "f"((float)w));  // w is normal
+        asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(s) : "f"(-0.2f * l));
         double y = (double)s;
 #pragma unroll
         for (int it = 0; it < 2; ++it) {
@@ -318,12 +320,29 @@ template <> struct Prec<float> {
         asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
         return r;
     }
-    static __device__ __forceinline__ float pow02(float v) { return ex2(0.2f * __log2f(v)); }
-    static __device__ __forceinline__ float powm08(float v) { return ex2(-0.8f * __log2f(v)); }
+    // log2 v by the lg2.approx instruction, flush-to-zero form: the
+    // arguments here are 0 or normal numbers (coordinates are sums and
+    // products of uniform fractions and bin widths, and the power map
+    // floors p at the smallest normal), on which it equals the form with
+    // subnormal support and skips that form's rescaling steps
+    static __device__ __forceinline__ float lg2(float v)
+    {
+        float r;
+        asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+        return r;
+    }
+    static __device__ __forceinline__ float pow02(float v) { return ex2(0.2f * lg2(v)); }
+    static __device__ __forceinline__ float powm08(float v) { return ex2(-0.8f * lg2(v)); }
     static __device__ __forceinline__ float exp2_(float v) { return ex2(v); }
-    // Jacobian factors of the FP32-eval form: reciprocal-based quotient
-    // (within 2 ulp for the normal denominators that occur here)
-    static __device__ __forceinline__ float div(float a, float b) { return __fdividef(a, b); }
+    // Jacobian factors of the FP32-eval form: a (1/b) by the div.approx
+    // instruction (within 2 ulp for |b| in [2^-126, 2^126]), flush-to-zero
+    // form: the denominators and quotients that occur here are normal
+    static __device__ __forceinline__ float div(float a, float b)
+    {
+        float r;
+        asm("div.approx.ftz.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+        return r;
+    }
     static __device__ __forceinline__ float tiny() { return 1.17549435e-38f; }
     static __device__ __forceinline__ bool le(float e, float x) { return e <= x; }
     // floor(x L) of x clamped to [0, 1], in [0, L]: x L + 2^23 rounded toward

@@ -242,8 +242,8 @@ __global__ void __launch_bounds__(PASS_THREADS, MINB) k_union(Params P, PassArgs
                 for (int s = nb; s < ne; ++s) {
                     const float4 r = ch.slot[s];
                     const float pk = Pt[__float_as_int(r.w)];
-                    lp += __log2f(pk);
-                    if (with_f) lq += __log2f(pk + r.x);
+                    lp += Prec<float>::lg2(pk);
+                    if (with_f) lq += Prec<float>::lg2(pk + r.x);
                     const float u = pk - gc;
                     as = fmaf(u, u, as);  // Σ (p_k - c)², times k2 once per channel
                 }

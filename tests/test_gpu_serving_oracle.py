@@ -127,15 +127,20 @@ def collider_state(oracle_mod):
     return pr, o, o.get_state()
 
 
-def test_fp32_generation_against_oracle(oracle_mod, collider_state):
+@pytest.mark.parametrize("family", ["k_union", "k_pass"])
+def test_fp32_generation_against_oracle(oracle_mod, collider_state, family):
+    """FP32-eval generation by each kernel family (union tables and staged
+    tiles) against the oracle's events on the collider."""
     from scipy import stats
     from paper_1811_09711_gb300 import vamp as V
     pr, o, st = collider_state
     n_ev = 6000
     g = V.Vamp(pr, precision=V.PREC_FP32_EVAL)
+    g.select_family(family)
     g.set_state(st["edges"], st["alpha"], st["shift"], st["w_max"])
     # same random stream: the oracle's events up to flipped accept decisions
     p_g, w_g, s_g = g.generate_torch(n_ev, gen_id=3)
+    assert g.kernel_name(1).startswith(family + "<float, 1,"), g.kernel_name(1)
     o.set_state(w_max=st["w_max"], have_pass=True)
     ev_o = o.generate(n_ev, gen_id=3)
     assert s_g["n_written"] == ev_o["n_written"] == n_ev
@@ -147,6 +152,7 @@ def test_fp32_generation_against_oracle(oracle_mod, collider_state):
     assert near >= 0.99
     # independent streams: acceptance rates and marginals
     g2 = V.Vamp(pr, precision=V.PREC_FP32_EVAL)
+    g2.select_family(family)
     g2.set_state(st["edges"], st["alpha"], st["shift"], st["w_max"])
     p2, _, s2 = g2.generate_torch(n_ev, gen_id=11)
     o.set_state(w_max=st["w_max"], have_pass=True)
