@@ -22,11 +22,12 @@
 //      (0 for the own and for switched-off channels) into shared memory, and
 //      the matching integrand peak -- one reciprocal and at most two
 //      exponentials per channel;
-//   U  per warp, its 32 calls transposed: lane l multiplies the densities of
-//      channels 2l, 2l+1 on every coordinate (one float2 of the call's row,
+//   U  per warp, its 32 calls transposed, two calls per warp load: lane
+//      (h, q) of half-warp h multiplies the densities of channels 4q..4q+3
+//      of call 2j+h on every coordinate (one float4 of the call's row,
 //      through L1, packed FP32x2 products) into the factors of J; a
-//      reduce-scatter over the lanes leaves Σ_c α_c g_c/φ'_c of call i in
-//      lane i;
+//      reduce-scatter over each half-warp and one shuffle leave
+//      Σ_c α_c g_c/φ'_c of call i in lane i;
 //   C  weights; integration: shifted sums per warp and each call's w^2 added
 //      to its d bins in global memory (FP64 reductions, no CTA barrier in
 //      the batch loop); generation: acceptance and ordered compaction.
@@ -74,15 +75,18 @@ __host__ __device__ constexpr UnionSmem union_smem_layout(int DM, int d, int n, 
     return UnionSmem{ds, js, ps, us, ch, bytes};
 }
 
-// One float2 of a density row, through L1 with the evict_unchanged
-// priority.  Measured on the collider pass (1e7 calls, after an L2 flush /
-// warm): 5.61 / 5.59 ms, against 5.91 / 5.62 ms without allocating in L1,
-// 5.93 / 5.62 ms with evict_first and 5.75 / 5.73 ms with the default
-// policy: calls cluster, so the warps of an SM share rows.
-__device__ __forceinline__ float2 ld_row(const float2* p)
+// One float4 of a density row, through L1 with the evict_unchanged
+// priority.  Measured on the collider pass with float2 loads (1e7 calls,
+// after an L2 flush / warm): 5.61 / 5.59 ms, against 5.91 / 5.62 ms
+// without allocating in L1, 5.93 / 5.62 ms with evict_first and
+// 5.75 / 5.73 ms with the default policy: calls cluster, so the warps of
+// an SM share rows.
+__device__ __forceinline__ float4 ld_row(const float4* p)
 {
-    float2 v;
-    asm("ld.global.nc.L1::evict_unchanged.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
+    float4 v;
+    asm("ld.global.nc.L1::evict_unchanged.v4.f32 {%0, %1, %2, %3}, [%4];"
+        : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+        : "l"(p));
     return v;
 }
 
@@ -263,30 +267,38 @@ __global__ void __launch_bounds__(PASS_THREADS, MINB) k_union(Params P, PassArgs
         }
         __syncwarp();
 
-        // ---- U: densities of the warp's calls, channels 2l and 2l+1 in lane l --
+        // ---- U: densities of the warp's calls: half-warp h takes calls 2j+h
+        // (j = 0..15), its lane q channels 4q..4q+3 --------------------------
         {
-            float2 acc[32];
+            const int h = lane >> 4, q = lane & 15;
+            float2 lo[16], hi[16];  // channels 4q, 4q+1 and 4q+2, 4q+3 of call 2j+h
 #pragma unroll
-            for (int i = 0; i < 32; ++i) acc[i] = *reinterpret_cast<const float2*>(Jw + i * UNION_JSTR + 2 * lane);
+            for (int j = 0; j < 16; ++j) {
+                const float* jr = Jw + (2 * j + h) * UNION_JSTR + 4 * q;
+                lo[j] = *reinterpret_cast<const float2*>(jr);
+                hi[j] = *reinterpret_cast<const float2*>(jr + 2);
+            }
 #pragma unroll 1
             for (int k = 0; k < d; ++k) {
-                const float2* row = reinterpret_cast<const float2*>(P.uD + (size_t)k * P.uMax * UNION_SLOTS) + lane;
-                const uint16_t* uk = Uw + k * 32;
+                const float4* row = reinterpret_cast<const float4*>(P.uD + (size_t)k * P.uMax * UNION_SLOTS) + q;
+                const uint16_t* uk = Uw + k * 32 + h;  // interval of call 2j+h at uk[2j]
 #pragma unroll
-                for (int i = 0; i < 32; ++i) {
-                    acc[i] = __fmul2_rn(acc[i], ld_row(row + (size_t)uk[i] * (UNION_SLOTS / 2)));  // packed FP32x2
+                for (int j = 0; j < 16; ++j) {
+                    const float4 r = ld_row(row + (size_t)uk[2 * j] * (UNION_SLOTS / 4));
+                    lo[j] = __fmul2_rn(lo[j], make_float2(r.x, r.y));  // packed FP32x2
+                    hi[j] = __fmul2_rn(hi[j], make_float2(r.z, r.w));
                 }
             }
-            float v[32];
+            float v[16];
 #pragma unroll
-            for (int i = 0; i < 32; ++i) v[i] = acc[i].x + acc[i].y;
-            // reduce-scatter: in the step of width s each lane trades half of
-            // its partial sums with lane ^ s (the lane with bit s set keeps
-            // the upper half), so that after five steps v[0] is the sum over
-            // all lanes for call `lane`
+            for (int j = 0; j < 16; ++j) v[j] = (lo[j].x + lo[j].y) + (hi[j].x + hi[j].y);
+            // reduce-scatter within the half-warp: in the step of width s
+            // each lane trades half of its partial sums with lane ^ s (the
+            // lane with bit s set keeps the upper half), so that after four
+            // steps v[0] of lane (h, q) is the sum over the half for call 2q+h
 #pragma unroll
-            for (int s = 16; s >= 1; s >>= 1) {
-                const bool up = (lane & s) != 0;
+            for (int s = 8; s >= 1; s >>= 1) {
+                const bool up = (q & s) != 0;
 #pragma unroll
                 for (int j = 0; j < s; ++j) {
                     const float send = up ? v[j] : v[j + s];
@@ -294,7 +306,8 @@ __global__ void __launch_bounds__(PASS_THREADS, MINB) k_union(Params P, PassArgs
                     v[j] = keep + __shfl_xor_sync(0xffffffffu, send, s);
                 }
             }
-            C.g[0] += v[0];
+            // call `lane` = 2q+h sits in lane 16h + q
+            C.g[0] += __shfl_sync(0xffffffffu, v[0], ((lane & 1) << 4) | (lane >> 1));
         }
         C.f[0] = f;
 #pragma unroll
