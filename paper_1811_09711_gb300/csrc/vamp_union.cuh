@@ -20,8 +20,8 @@
 //      two halves of part J, so that the reads of U_k overlap it);
 //   J  per channel c: α_c × the Jacobians of its mapped coordinates at p
 //      (0 for the own and for switched-off channels) into shared memory, and
-//      the matching integrand peak -- one reciprocal and at most two
-//      exponentials per channel;
+//      the matching integrand peak -- one quotient and two exponentials
+//      per channel;
 //   U  per warp, its 32 calls transposed, two calls per warp load: lane
 //      (h, q) of half-warp h multiplies the densities of channels 4q..4q+3
 //      of call 2j+h on every coordinate (one float4 of the call's row,
@@ -45,7 +45,7 @@ constexpr int UNION_JSTR = UNION_SLOTS + 2;  // floats per call row of the chann
 // numerators Γ/A; and its mapped coordinates, the nbw Breit-Wigner ones
 // first (m, Γ², -, k), then the npw power-law ones (δ, -, -, k), so that
 // part J runs two loops of uniform trip count with no test of the map kind.
-// A channel's factors are formed with one reciprocal and two exponentials:
+// A channel's factors are formed with one quotient and two exponentials:
 // its Breit-Wigner Jacobians Γ/(A((p-m)² + Γ²)) as the constant over the
 // product of the denominators (each at least Γ² >= 1e-8, so the product of
 // four stays a normal FP32 number), its power-law Jacobians
@@ -53,7 +53,7 @@ constexpr int UNION_JSTR = UNION_SLOTS + 2;  // floats per call row of the chann
 // factors Π (p + δ)^(-4/5) joined to its Gaussian exponent.
 struct UnionChan {
     float alpha, wz, jc;  // α_c 0.2^npw, the peak weight Π 1/powN, Π_BW Γ/A
-    int nslot;            // nbw | npw << 8
+    int nslot;            // nbw | (nbw + npw) << 8: the Breit-Wigner slots and the end of the power-law ones
     float4 slot[MAXMAP];  // {c0, c1, -, bits of k}
 };
 static_assert(sizeof(UnionChan) == 80, "UnionChan layout");
@@ -159,7 +159,7 @@ __global__ void __launch_bounds__(PASS_THREADS, MINB) k_union(Params P, PassArgs
         ucs[c].alpha = P.alpha32[c] * a5;
         ucs[c].wz = wz;
         ucs[c].jc = jc;
-        ucs[c].nslot = nb | (np << 8);
+        ucs[c].nslot = nb | ((nb + np) << 8);
     }
     __syncthreads();
 
@@ -231,7 +231,7 @@ __global__ void __launch_bounds__(PASS_THREADS, MINB) k_union(Params P, PassArgs
 #pragma unroll 4
             for (int c2 = c_lo; c2 < c_hi; ++c2) {
                 const UnionChan& ch = ucs[c2];
-                const int nb = ch.nslot & 0xff, ne = nb + (ch.nslot >> 8);
+                const int nb = ch.nslot & 0xff, ne = ch.nslot >> 8;
                 float den = 1.f, as = 0.f, lp = 0.f, lq = 0.f;
 #pragma unroll 1
                 for (int s = 0; s < nb; ++s) {
@@ -251,11 +251,10 @@ __global__ void __launch_bounds__(PASS_THREADS, MINB) k_union(Params P, PassArgs
                     const float u = pk - gc;
                     as = fmaf(u, u, as);  // Σ (p_k - c)², times k2 once per channel
                 }
-                const float bw = Prec<float>::div(1.f, den);  // Π_BW ((p-m)² + Γ²)^-1
-                const float jb = ch.jc * bw;  // Π_BW 1/φ'
-                const float J = jb * (ne > nb ? Prec<float>::exp2_(-0.8f * lp) : 1.f);
+                const float jb = Prec<float>::div(ch.jc, den);  // Π_BW 1/φ' = Π_BW Γ/A over Π_BW ((p-m)² + Γ²)
+                const float J = jb * Prec<float>::exp2_(-0.8f * lp);  // lp = 0 without power-law slots
                 const float a = ch.alpha;
-                Jw[lane * UNION_JSTR + c2] = (a != 0.f && c2 != own) ? a * J : 0.f;
+                Jw[lane * UNION_JSTR + c2] = a != 0.f ? a * J : 0.f;  // the own channel's is cleared below
                 if (with_f) f += ch.wz * Prec<float>::exp2_(fmaf(-0.8f, lq, fmaf(as, k2, -Aq))) * jb;
             }
             if (half == 0) {
@@ -265,6 +264,8 @@ __global__ void __launch_bounds__(PASS_THREADS, MINB) k_union(Params P, PassArgs
                     if (sh.has(k)) Uw[k * 32 + lane] = (uint16_t)union_interval(P, k, Pt[k], ce[k]);
             }
         }
+        // the own channel's term is in g already (phase A)
+        if ((unsigned)own < (unsigned)K) Jw[lane * UNION_JSTR + own] = 0.f;
         __syncwarp();
 
         // ---- U: densities of the warp's calls: half-warp h takes calls 2j+h
