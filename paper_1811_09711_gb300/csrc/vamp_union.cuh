@@ -117,6 +117,7 @@ __global__ void __launch_bounds__(PASS_THREADS, MINB) k_union(Params P, PassArgs
     constexpr int DM = SH::DM;
     constexpr int PSTR = union_pstride(DM);
     constexpr int NW = PASS_THREADS / 32;
+    static_assert(union_smem_layout(DM, 1, 1, MODE).us % 16 == 0, "part U reads the intervals as 16-byte words");
     extern __shared__ __align__(128) unsigned char smem[];
     SmemHead& H = *reinterpret_cast<SmemHead*>(smem);
     const SH sh(P.lay32, P.d, P.n);
@@ -279,15 +280,28 @@ __global__ void __launch_bounds__(PASS_THREADS, MINB) k_union(Params P, PassArgs
                 lo[j] = *reinterpret_cast<const float2*>(jr);
                 hi[j] = *reinterpret_cast<const float2*>(jr + 2);
             }
+            // the intervals of calls 2j and 2j+1 share 32-bit word j (low and
+            // high half); a lane takes its half with one byte permute
+            const uint32_t sel = h ? 0x4432u : 0x4410u;
 #pragma unroll 1
             for (int k = 0; k < d; ++k) {
                 const float4* row = reinterpret_cast<const float4*>(P.uD + (size_t)k * P.uMax * UNION_SLOTS) + q;
-                const uint16_t* uk = Uw + k * 32 + h;  // interval of call 2j+h at uk[2j]
+                // the warp's 32 intervals of coordinate k: 64 bytes at a 16-byte
+                // boundary (the layout rounds every region to 16 bytes and a
+                // warp's block is DM * 64 bytes), four broadcast loads
+                const uint4* uw = reinterpret_cast<const uint4*>(Uw + k * 32);
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const float4 r = ld_row(row + (size_t)uk[2 * j] * (UNION_SLOTS / 4));
-                    lo[j] = __fmul2_rn(lo[j], make_float2(r.x, r.y));  // packed FP32x2
-                    hi[j] = __fmul2_rn(hi[j], make_float2(r.z, r.w));
+                for (int j4 = 0; j4 < 4; ++j4) {
+                    const uint4 w = uw[j4];
+                    const uint32_t wv[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        const int j = 4 * j4 + t;
+                        const uint32_t u = __byte_perm(wv[t], 0u, sel);  // interval of call 2j+h
+                        const float4 r = ld_row(row + (size_t)u * (UNION_SLOTS / 4));
+                        lo[j] = __fmul2_rn(lo[j], make_float2(r.x, r.y));  // packed FP32x2
+                        hi[j] = __fmul2_rn(hi[j], make_float2(r.z, r.w));
+                    }
                 }
             }
             float v[16];
