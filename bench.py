@@ -271,13 +271,13 @@ def union_xu_ops_per_call(pr) -> float:
 def union_lsu_wavefronts_per_call(pr) -> float:
     """Shared-memory wavefronts of one call in the union pass at one per warp
     access: per channel its record and per mapped coordinate the slot record
-    and the call's coordinate (part J, per thread); per coordinate and pair
-    of calls the word holding both calls' intervals (part U: a warp load
-    serves two calls); the channel factors written (two wavefronts per warp
-    store of 32 calls) and read back (two per float2 warp load)."""
+    and the call's coordinate (part J, per thread); per coordinate the 32
+    intervals of the warp's calls (part U: four 16-byte broadcast loads per
+    32 calls); the channel factors written (two wavefronts per warp store of
+    32 calls) and read back (two per float2 warp load)."""
     mapped = int(sum(int(x) for x in pr.channels.n_mapped))
     K = pr.n_channels
-    return (K + 2.0 * mapped) / 32.0 + pr.d / 2.0 + 2.0 * K / 32.0 + 2.0
+    return (K + 2.0 * mapped) / 32.0 + pr.d * 4.0 / 32.0 + 2.0 * K / 32.0 + 2.0
 
 
 def fp64_form_ops_per_call(pr) -> float:

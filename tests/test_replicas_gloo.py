@@ -93,6 +93,22 @@ def test_roofline_per_pipe_work():
     assert bench.fp64_ops_per_call(pr) == 20.0
 
 
+def test_union_pass_per_pipe_work():
+    """Per-pipe work per call of the union pass, term by term: L2 bytes (one
+    256-byte density row and one 4-byte cell entry per coordinate), MUFU
+    operations (one exp2 per channel, one reciprocal per Breit-Wigner map,
+    four per power map) and shared-memory wavefronts (channel record, slot
+    record and coordinate per mapped slot; four 16-byte interval loads per
+    coordinate and 32 calls; the factors written and read back)."""
+    import bench
+    from paper_1811_09711_gb300 import problems as P
+    pr = P.collider()
+    bw, pw = bench.mapped_kinds(pr)
+    assert bench.union_l2_bytes_per_call(pr) == 14 * (256 + 4) == 3640
+    assert bench.union_xu_ops_per_call(pr) == 64 + bw + 4 * pw
+    assert bench.union_lsu_wavefronts_per_call(pr) == (64 + 2 * 188) / 32 + 14 * 4 / 32 + 2 * 64 / 32 + 2 == 21.5
+
+
 def test_fp64_form_operation_count():
     """Floating-point work per call of the FP64 form, term by term: one
     density product per lookup, 12 per Breit-Wigner map, 14 per power map,
